@@ -1,0 +1,286 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test would fail under a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a wrong factor).  No GPU needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1310_0998_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def P(orc, **kw):
+    base = dict(L=10.0, a=25.0, gamma=4.5, kBT=1.0, rc=1.0, kbond=100.0, r0=0.5, fp=1.0,
+                zeta=0.1, dt=0.01, mass=1.0, seed=0, exclude_bonded=1, noise=0)
+    base.update(kw)
+    return orc.params(**base)
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10
+# --------------------------------------------------------------------------
+
+def test_philox_matches_triton_interpreter(orc, tmp_path):
+    """Triton ships an independent Philox4x32-10 (tl.philox); its CPU
+    interpreter evaluates it with numpy.  The oracle must agree bit for bit."""
+    pytest.importorskip("triton")
+    import subprocess
+    import sys
+
+    rng = np.random.default_rng(7)
+    n = 256
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    helper = os.path.join(os.path.dirname(__file__), "triton_philox_ref.py")
+    for k, seed in enumerate((0, 0x123456789ABCDEF, 2**64 - 1)):
+        path = str(tmp_path / f"ctr{k}.npz")
+        np.savez(path, ctr=ctr, seed=np.uint64(seed))
+        env = dict(os.environ, TRITON_INTERPRET="1")
+        subprocess.run([sys.executable, helper, path], check=True, env=env, timeout=600)
+        tri = np.load(path + ".out.npy")
+        ours = orc.philox(ctr, (seed & 0xFFFFFFFF, seed >> 32))
+        np.testing.assert_array_equal(ours, tri)
+
+
+def test_philox_uniformity_and_alpha_moments(orc):
+    n = 1 << 20
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 2] = 12345
+    w = orc.philox(ctr, (0xDEADBEEF, 0x1234))
+    u = ((w[:, 0] >> 8).astype(np.float64) + 0.5) / 2**24
+    assert abs(u.mean() - 0.5) < 3e-4 * 4
+    assert abs(u.var() - 1.0 / 12.0) < 2e-4
+    hist = np.bincount((w[:, 1] >> 24).astype(np.int64), minlength=256)
+    chi2 = float(((hist - n / 256) ** 2 / (n / 256)).sum())
+    assert chi2 < 255 + 6 * math.sqrt(2 * 255)
+    # the alpha mapping: zero mean, unit variance, symmetric in (i, j)
+    a = np.array([orc.alpha(i, i + 1 + (i % 7), 3, 99) for i in range(20000)])
+    assert abs(a.mean()) < 4 / math.sqrt(20000)
+    assert abs(a.var() - 1.0) < 0.03
+    assert np.abs(a).max() < math.sqrt(3.0)
+    for i, j in [(0, 1), (5, 900), (123456, 7)]:
+        assert orc.alpha(i, j, 17, 5) == orc.alpha(j, i, 17, 5)
+        assert orc.alpha(i, j, 17, 5) != orc.alpha(i, j, 18, 5)
+        assert orc.alpha(i, j, 17, 5) != orc.alpha(i, j, 17, 6)
+    g = np.array([orc.alpha(i, 2 * i + 3, 1, 4, noise=1) for i in range(20000)])
+    assert abs(g.mean()) < 4 / math.sqrt(20000)
+    assert abs(g.var() - 1.0) < 0.04
+    assert abs(float(np.mean(g ** 4)) - 3.0) < 0.25
+
+
+# --------------------------------------------------------------------------
+# Pair force, hand-derived (golden fixtures)
+# --------------------------------------------------------------------------
+
+def test_pair_force_golden_cases(orc):
+    cases = json.load(open(os.path.join(GOLDEN, "pair_cases.json")))["cases"]
+    for c in cases:
+        p = P(orc, L=c["L"], a=c["a"], gamma=c["gamma"], kBT=c["kBT"], rc=c["rc"], exclude_bonded=0)
+        f = orc.pair_forces_only(p, np.array(c["x"]), np.array(c["v"]), 1)
+        np.testing.assert_allclose(f[0], c["f0"], atol=1e-12, err_msg=c["name"])
+        np.testing.assert_allclose(f[1], -np.array(c["f0"]), atol=1e-12, err_msg=c["name"])
+
+
+def test_random_force_scaling(orc):
+    """f_R = sqrt(2 gamma kBT) w alpha dt^-1/2 e: pure random part with A = 0
+    and zero velocities scales as sqrt(gamma kBT / dt); its direction is e."""
+    x = np.array([[5.0, 5.0], [5.0, 5.6]])
+    v = np.zeros((2, 2))
+    base = orc.pair_forces_only(P(orc, a=0.0, gamma=2.0, kBT=1.0, dt=0.01, exclude_bonded=0), x, v, 9)
+    assert abs(base[0, 0]) < 1e-14 and abs(base[0, 1]) > 0
+    al = orc.alpha(0, 1, 9, 0)
+    np.testing.assert_allclose(base[0, 1], -math.sqrt(2 * 2.0 * 1.0) * 0.4 * al / math.sqrt(0.01), rtol=1e-13)
+    f2 = orc.pair_forces_only(P(orc, a=0.0, gamma=8.0, kBT=1.0, dt=0.04, exclude_bonded=0), x, v, 9)
+    np.testing.assert_allclose(f2, base, rtol=1e-13)   # 4x gamma, 4x dt
+    f3 = orc.pair_forces_only(P(orc, a=0.0, gamma=2.0, kBT=4.0, dt=0.01, exclude_bonded=0), x, v, 9)
+    np.testing.assert_allclose(f3, 2 * base, rtol=1e-13)
+
+
+def test_bonded_pair_switched_off_and_superposition(orc):
+    """Sec. 2.2: no pair force inside a dimer; pair forces superpose."""
+    x = np.array([[5.0, 5.0], [5.4, 5.0], [5.0, 5.7], [8.0, 8.0]])
+    v = np.zeros((4, 2))
+    p_on = P(orc, gamma=0.0, kBT=0.0, exclude_bonded=1)
+    f = orc.pair_forces_only(p_on, x, v, 1)
+    # bead 0 sees only bead 2 (bead 1 is its partner): r = 0.7, w = 0.3, e = -y
+    np.testing.assert_allclose(f[0], [0.0, -25 * 0.3], atol=1e-12)
+    # bead 1 sees bead 2: d = (0.4, -0.7), r = 0.806..., beyond? r < 1
+    d = np.array([0.4, -0.7]); r = np.hypot(*d)
+    np.testing.assert_allclose(f[1], 25 * (1 - r) * d / r, atol=1e-12)
+    np.testing.assert_allclose(f[3], [0, 0], atol=1e-14)
+    p_off = P(orc, gamma=0.0, kBT=0.0, exclude_bonded=0)
+    f_off = orc.pair_forces_only(p_off, x, v, 1)
+    np.testing.assert_allclose(f_off[0] - f[0], [-25 * 0.6, 0.0], atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Dynamics: conservation laws and closed forms
+# --------------------------------------------------------------------------
+
+def _bead_momentum(v):
+    return v.sum(axis=0)
+
+
+def test_momentum_conserved_without_drag_and_propulsion(orc):
+    x, _ = synth.dimers(128, 12.0, 0.5, seed=3)
+    v = synth.velocities(256, 1.0, seed=4).astype(np.float64)
+    p = P(orc, L=12.0, zeta=0.0, fp=0.0)
+    st = orc.State(p, x, v, step=0)
+    P0 = _bead_momentum(st.v).copy()
+    scale = np.abs(st.v).sum()
+    st.run(1000)
+    assert np.abs(_bead_momentum(st.v) - P0).max() <= 1e-10 * scale
+
+
+def test_discrete_momentum_balance(orc):
+    """With drag and propulsion: pair and bond forces cancel, so the total
+    force is sum_k 2 f_p n_k - zeta sum_i v_i(half step).  With the per-step
+    log, v_half = v_{s+1} - (dt/2m) f_{s+1} gives
+    sum F_{s+1} (1 - zeta dt / 2m) = 2 f_p sum_k n_k - zeta P_{s+1}."""
+    L = 12.0
+    x, v = synth.dimers(128, L, 0.5, seed=5)
+    p = P(orc, L=L, zeta=0.7, fp=1.3, dt=0.01)
+    st = orc.State(p, x, v)
+    for _ in range(5):
+        log = st.run(20, thermo=True)
+        xh, xt = st.x[0::2], st.x[1::2]
+        d = xh - xt
+        d -= L * np.rint(d / L)
+        n = d / np.linalg.norm(d, axis=1)[:, None]
+        lhs = log[-1, 3:5] * (1 - 0.7 * 0.01 / 2)
+        rhs = 2 * 1.3 * n.sum(axis=0) - 0.7 * log[-1, 1:3]
+        np.testing.assert_allclose(lhs, rhs, atol=1e-9 * (1 + np.abs(rhs).max()))
+        # integrator bookkeeping: P_{s+1} - P_s = dt/2 (F_s + F_{s+1})
+        dP = log[1:, 1:3] - log[:-1, 1:3]
+        np.testing.assert_allclose(dP, 0.005 * (log[1:, 3:5] + log[:-1, 3:5]), atol=1e-10)
+
+
+def test_continuous_momentum_balance(orc):
+    """dP/dt = sum F_p - zeta P (spec form), to O(dt^2)."""
+    L = 12.0
+    x, v = synth.dimers(100, L, 0.5, seed=8)
+    zeta, fp, dt = 0.5, 1.0, 0.005
+    p = P(orc, L=L, zeta=zeta, fp=fp, dt=dt)
+    st = orc.State(p, x, v)
+    st.run(50)
+    P0 = st.v.sum(axis=0).copy()
+    xh, xt = st.x[0::2], st.x[1::2]
+    d = xh - xt; d -= L * np.rint(d / L)
+    Fp = 2 * fp * (d / np.linalg.norm(d, axis=1)[:, None]).sum(axis=0)
+    st.run(1)
+    dPdt = (st.v.sum(axis=0) - P0) / dt
+    np.testing.assert_allclose(dPdt, Fp - zeta * P0, atol=0.02 * (1 + np.abs(Fp).max()))
+
+
+def test_single_dimer_drift_speed(orc):
+    """One dimer alone: both beads feel f_p n - zeta v, the bond stays at
+    rest, and the speed obeys the velocity-Verlet recurrence with the drag on
+    the half-step velocity; it tends to the terminal speed f_p/zeta."""
+    L, r0, fp, zeta, dt = 32.0, 0.5, 1.0, 0.1, 0.01
+    th = 0.3
+    c = np.array([10.0, 12.0])
+    h = 0.5 * r0 * np.array([math.cos(th), math.sin(th)])
+    x = np.array([c + h, c - h])
+    v = np.zeros((2, 2))
+    p = P(orc, L=L, r0=r0, fp=fp, zeta=zeta, dt=dt)
+    st = orc.State(p, x, v)
+    # scalar recurrence along n (not the oracle's code: one particle, one force)
+    u, fcur, hh = 0.0, fp, 0.5 * dt
+    for _ in range(3000):
+        uh = u + hh * fcur
+        fcur = fp - zeta * uh
+        u = uh + hh * fcur
+    st.run(3000)
+    n = np.array([math.cos(th), math.sin(th)])
+    np.testing.assert_allclose(st.v[0] @ n, u, rtol=1e-12)
+    np.testing.assert_allclose(st.v[1], st.v[0], atol=1e-12)
+    st.run(20000)
+    assert abs(st.v[0] @ n - fp / zeta) < 1e-3 * fp / zeta
+
+
+def test_bond_oscillation_frequency(orc):
+    """Two beads on a spring kappa: the separation oscillates about r0 with
+    omega = sqrt(2 kappa / m) (reduced mass m/2), Eq. (stiffSpring)."""
+    kb, r0, dt, delta = 100.0, 0.5, 0.001, 0.05
+    x = np.array([[5.0 + 0.5 * (r0 + delta), 5.0], [5.0 - 0.5 * (r0 + delta), 5.0]])
+    p = P(orc, L=10.0, kbond=kb, r0=r0, fp=0.0, zeta=0.0, gamma=0.0, kBT=0.0, dt=dt)
+    st = orc.State(p, x, np.zeros((2, 2)))
+    seps = []
+    for _ in range(2000):
+        st.run(1)
+        seps.append(st.x[0, 0] - st.x[1, 0] - r0)
+    seps = np.array(seps)
+    t = (np.arange(len(seps)) + 1) * dt
+    crossings = t[1:][np.sign(seps[1:]) != np.sign(seps[:-1])]
+    period = 2 * np.mean(np.diff(crossings))
+    omega = math.sqrt(2 * kb)
+    assert abs(period - 2 * math.pi / omega) < 2e-3 * (2 * math.pi / omega)
+    assert abs(np.abs(seps).max() - delta) < 2e-3
+
+
+@pytest.mark.slow
+def test_equilibrium_temperature(orc):
+    """zeta = f_p = 0: the DPD thermostat holds T = kBT (fluctuation-
+    dissipation sigma^2 = 2 gamma kBT, w_D = w_R^2; Sec. 2.1).  C1 geometry."""
+    L = 32.0
+    x, v = synth.dimers(512, L, 0.5, seed=0)
+    p = P(orc, L=L, zeta=0.0, fp=0.0, seed=11)
+    st = orc.State(p, x, v, cells=True)
+    st.run(2000)
+    log = st.run(18000, thermo=True)
+    n = x.shape[0]
+    T = 2 * log[:, 0] / (2 * n - 2)
+    assert abs(T.mean() - 1.0) < 0.02, T.mean()
+
+
+def test_cell_list_variant_matches_all_pairs(orc):
+    L = 9.0
+    x, _ = synth.dimers(150, L, 0.5, seed=2)
+    v = synth.velocities(300, 1.0, seed=2)
+    p = P(orc, L=L)
+    f1, n1 = orc.forces(p, x.astype(np.float64), v.astype(np.float64), 4)
+    f2, n2 = orc.forces(p, x.astype(np.float64), v.astype(np.float64), 4, cells=True)
+    assert n1 == n2
+    np.testing.assert_allclose(f2, f1, atol=1e-11)
+
+
+def test_cell_rule_stencil_is_sufficient(orc):
+    """With n_c = floor(L / (r_c + 2^-20 L)) cells per side and the FP32
+    binning rule, every interacting pair sits in the same or an adjacent cell
+    (periodically), so a 3x3 stencil finds all pairs."""
+    for L, seed in [(3.0, 0), (7.0, 1), (32.0, 2), (1024.0, 3)]:
+        nc = int(math.floor(L / (1.0 + 2.0 ** -20 * L)))
+        rng = np.random.default_rng(seed)
+        n = 400
+        x = (rng.random((n, 2)) * L).astype(np.float32)
+        # put pairs straddling cell edges at just under r_c
+        edges = (np.arange(min(nc, 50)) * np.float32(L / nc)).astype(np.float32)
+        k = len(edges)
+        x[:k, 0] = edges + np.float32(1e-6 * L)
+        x[k:2 * k, 0] = np.mod(x[:k, 0] + np.float32(0.9999), np.float32(L))
+        x[k:2 * k, 1] = x[:k, 1]
+        x[x >= np.float32(L)] = 0
+        cnt = orc.cell_counts(x, L, nc)
+        assert cnt.sum() == n
+        inv = np.float32(nc) / np.float32(L)
+        cx = np.minimum(nc - 1, (x[:, 0] * inv).astype(np.int64))
+        cy = np.minimum(nc - 1, (x[:, 1] * inv).astype(np.int64))
+        cs = L / nc
+        # each bead lies in its cell up to FP32 rounding of the product
+        assert np.all(x[:, 0] >= cx * cs - 1e-6 * L) and np.all(x[:, 0] <= (cx + 1) * cs + 1e-6 * L)
+        xd = x.astype(np.float64)
+        d = xd[:, None, :] - xd[None, :, :]
+        d -= L * np.rint(d / L)
+        r2 = (d ** 2).sum(-1)
+        ii, jj = np.nonzero(np.triu(r2 < 1.0, 1))
+        ddx = np.abs(cx[ii] - cx[jj]); ddx = np.minimum(ddx, nc - ddx)
+        ddy = np.abs(cy[ii] - cy[jj]); ddy = np.minimum(ddy, nc - ddy)
+        assert ddx.max(initial=0) <= 1 and ddy.max(initial=0) <= 1
