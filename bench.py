@@ -1,0 +1,295 @@
+"""Benchmark: particle-steps/s of the DPD dimer hot path on one GB300.
+
+Workload (default, "c3"): periodic box L = 1024 (r_c = 1), bead density 3 ->
+3,145,728 beads (1,572,864 dimers) at random centres/orientations (seed 0),
+a = 25, gamma = 4.5, kBT = 1, kappa = 100, r0 = 0.5, f_p = 1, zeta = 0.1,
+dt = 0.01.  One step = one velocity-Verlet step of the whole system (cell
+scan, scatter, fused pair/bond/propulsion/drag force + integration + FP64
+thermo reduction).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the simulator's stream, with a 512 MiB write + read L2 flush between
+timed steps (outside the events).  value = beads * K / sum(step times).
+Under torchrun each rank runs an independent replica (no collective on the
+data path; "replicas only"), value = all ranks' bead-steps / max time.
+
+--impl reference times the FP64 CPU oracle (cell-list variant, OpenMP) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PHYS = dict(a=25.0, gamma=4.5, kBT=1.0, rc=1.0, kbond=100.0, r0=0.5, fp=1.0, zeta=0.1, dt=0.01, mass=1.0)
+CONFIGS = {
+    "c3": dict(L=1024.0, n_beads=3 * 1024 * 1024, name="c3: L=1024, density 3, 3,145,728 beads"),
+    "c2": dict(L=256.0, n_beads=3 * 256 * 256, name="c2-size: L=256, density 3, 196,608 beads"),
+    "c1": dict(L=32.0, n_beads=1024, name="c1: L=32, 512 dimers"),
+}
+OPS_PER_BEAD_STEP = 650.0      # algorithmic ALU operations per bead-step
+BYTES_PER_BEAD_STEP = 36.0     # algorithmic HBM bytes per bead-step (read 20, write 16)
+N_SM, LANES = 152, 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return dict(hbm=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), src="measured")
+    return dict(hbm=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if bus_id:
+            cmd.insert(1, f"--id={bus_id}")
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(L, n_beads, budget_s=12.0, seed=0):
+    """Time the FP64 cell-list oracle (OpenMP) on the host; returns
+    (bead-steps/s, threads, description of the sample)."""
+    import oracle
+    from paper_1310_0998_gb300 import synth
+    oracle.build()
+    x, v = synth.dimers(n_beads // 2, L, PHYS["r0"], seed=seed)
+    p = oracle.params(L=L, seed=seed, **PHYS)
+    st = oracle.State(p, x, v, cells=True)
+    t0 = time.perf_counter()
+    st.run(1)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-6)
+    more = max(1, int(budget_s / per) - 1)
+    st.run(more)
+    t2 = time.perf_counter()
+    steps = 1 + more
+    rate = n_beads * steps / (t2 - t0)
+    return rate, oracle.num_threads(), f"{steps} steps of the FP64 cell-list oracle on a {n_beads}-bead box (L={L:g}, density 3), {t2 - t0:.1f} s"
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # bounded sample: a density-3 sub-box whose oracle step is well under a second
+    Ls = 128.0 if cfg["n_beads"] > 200000 else cfg["L"]
+    nb = int(round(cfg["n_beads"] * (Ls / cfg["L"]) ** 2)) // 2 * 2
+    import oracle
+    from paper_1310_0998_gb300 import synth
+    oracle.build()
+    x, v = synth.dimers(nb // 2, Ls, PHYS["r0"], seed=0)
+    st = oracle.State(oracle.params(L=Ls, seed=0, **PHYS), x, v, cells=True)
+    st.run(args.warmup)
+    t0 = time.perf_counter()
+    st.run(args.steps)
+    dt = time.perf_counter() - t0
+    value = nb * args.steps / dt
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "bead_density": 3.0, "sample_beads": nb},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} steps of the FP64 cell-list oracle on a {nb}-bead sub-box (L={Ls:g}) of the same density and parameters"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1310_0998_gb300 import Sim, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    L, nb = cfg["L"], cfg["n_beads"]
+    stream = torch.cuda.Stream(device=dev)
+    x, v = synth.dimers(nb // 2, L, PHYS["r0"], seed=rank)
+    sim = Sim(L, nb, stream=stream.cuda_stream, seed=rank, a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"],
+              rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"],
+              dt=PHYS["dt"], mass=PHYS["mass"])
+    sim.set_positions(x, v)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.sync()
+    _, npairs = sim.pair_counts()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)     # 512 MiB
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def l2_flush(k):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            sink.add_(flush[:: 1 << 12].sum())
+
+    bus = None
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        bus = None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(bus)
+    evs = []
+    for k in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(1)
+        e1.record(stream)
+        evs.append((e0, e1))
+        l2_flush(k)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.sync()
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    t_dev = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+        dist.barrier()
+    value = world * nb * args.steps / t_dev
+
+    # per-kernel device times (same kernels, launched one by one between events)
+    prof = []
+    for k in range(min(args.steps, 20)):
+        prof.append(sim.profile_step())
+        l2_flush(k)
+        torch.cuda.synchronize()
+    prof = np.array(prof)
+    force_s = float(prof[:, 2].mean()) / 1e3
+
+    # end to end through the C ABI with host (pinned) buffers: upload the full
+    # state (x, v, f), one step, download it
+    xv_h = torch.empty((nb, 4), dtype=torch.float32, pin_memory=True).numpy()
+    f_h = torch.empty((nb, 2), dtype=torch.float32, pin_memory=True).numpy()
+    _, _, s_cur = sim.get_state(xv_h, f_h)
+    sim.set_state(xv_h, f_h, s_cur)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sim.set_state(xv_h, f_h, s_cur)
+        sim.step(1)
+        _, _, s_cur = sim.get_state(xv_h, f_h)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * nb * args.e2e_steps / e2e_s
+    info = sim.info()
+
+    pk = peaks()
+    alu_peak = N_SM * LANES * pk["sm_max_mhz"] * 1e6
+    alu_ach = OPS_PER_BEAD_STEP * nb / force_s
+    hbm_ach = BYTES_PER_BEAD_STEP * value / world / 1e9
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "beads": nb, "L": L, "bead_density": nb / L / L,
+                   "tile": info.tile, "l2": "512 MiB write+read flush between timed steps",
+                   "pairs_per_bead": npairs / nb, "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "kernel": "force_integrate", "achieved": alu_ach / 1e12,
+                     "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": None,
+                     "peak_src": f"{N_SM} SMs x {LANES} lanes x {pk['sm_max_mhz']:.0f} MHz",
+                     "ms": force_s * 1e3},
+        "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm"], "frac": hbm_ach / pk["hbm"],
+                "bytes_per_bead_step": BYTES_PER_BEAD_STEP, "peak_src": pk["src"]},
+        "kernels_ms": {"scan": float(prof[:, 0].mean()), "scatter": float(prof[:, 1].mean()),
+                       "force_integrate": float(prof[:, 2].mean())},
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s", "h2d_bytes_per_step": 24 * nb,
+                "d2h_bytes_per_step": 24 * nb, "steps": args.e2e_steps},
+        "gpu_launches": 3 * args.steps,
+        "overflow_tiles": int(info.overflow_tiles),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        Lc = 128.0 if nb > 200000 else L
+        nbc = int(round(nb * (Lc / L) ** 2)) // 2 * 2
+        rate, cores, sample = cpu_oracle_rate(Lc, nbc)
+        line["cpu_baseline"] = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

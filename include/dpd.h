@@ -1,0 +1,193 @@
+/*
+ * libdpd — GB300 (sm_103a) simulator of self-propelled DPD dimers
+ * (Hinz, Panchenko, Kim & Fried, arXiv:1310.0998).
+ *
+ * C ABI.  Every entry point returns an int status: DPD_OK (0) or a negative
+ * DPD_ERR_* code; dpd_status_string() names it.  Pointers are plain host or
+ * device addresses as stated per argument; nothing here takes a CUDA or torch
+ * type (streams are passed as void*, a cudaStream_t; NULL makes the context
+ * create and own a non-blocking stream).
+ *
+ * Model (Sec. 2): N beads of mass m in a periodic square of side L; beads 2k
+ * and 2k+1 form agent k (2k = head).  Force on bead i:
+ *   pair (Eqs. DPDf, DPDcdr, weightFunc01), r < r_c, bonded partner excluded:
+ *     [A w - gamma w^2 (v_ij.e) + sqrt(2 gamma kBT) w alpha_ij dt^-1/2] e,
+ *     w = 1 - r/r_c, e = (x_i - x_j)/r (minimum image);
+ *   bond (Eq. stiffSpring): -kappa (r - r0) e toward the partner's side;
+ *   propulsion (Eq. DPDnp): f_p n_k on each bead, n_k = head - tail, unit;
+ *   Stokes drag (Eq. DPDnp): -zeta v.
+ * Time stepping: standard velocity-Verlet (Sec. 5); the dissipative and drag
+ * terms see the half-step velocity; the set-up force of a fresh state sees v.
+ * alpha_ij: Philox4x32-10 (Salmon et al., SC'11), counter (min id, max id,
+ * step lo, step hi), key (seed lo, seed hi ^ replica), word 0 mapped to
+ * sqrt(3) (2 (w0 >> 8) + 1 - 2^24) 2^-24 (uniform, unit variance) or, with
+ * noise = 1, Box-Muller on words 0 and 1.
+ *
+ * State layout on the host side of the ABI: "xv" = float[N][4] (x, y, vx, vy)
+ * in id order, "f" = float[N][2] in id order.  FP32 state; FP64 reductions.
+ *
+ * Concurrency: a context is not thread-safe; all its work is ordered on its
+ * stream.  Calls that return host data synchronise that stream.  Device-side
+ * errors (non-finite state, a wait that timed out, an inconsistent cell list)
+ * are latched in device memory and returned by the next synchronising call
+ * (dpd_sync, any getter); dpd_step itself only reports launch errors.
+ */
+#ifndef DPD_H_
+#define DPD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DPD_OK 0
+#define DPD_ERR_INVALID_ARG (-1) /* a parameter or size failed validation      */
+#define DPD_ERR_CUDA (-2)        /* a CUDA runtime call failed                 */
+#define DPD_ERR_OOM (-3)         /* device allocation failed                   */
+#define DPD_ERR_NONFINITE (-4)   /* a position or velocity became non-finite   */
+#define DPD_ERR_TIMEOUT (-5)     /* a bounded device wait gave up              */
+#define DPD_ERR_STATE (-6)       /* call not valid in the context's state      */
+#define DPD_ERR_INTERNAL (-7)    /* cell list inconsistent (bounds check hit)  */
+
+#define DPD_HOST 0   /* pointer argument is a host address   */
+#define DPD_DEVICE 1 /* pointer argument is a device address */
+
+/* Model and run parameters (Sec. 2; nondimensional groups of Sec. 3 map onto
+ * them as A = Phi f0, kBT = f0 l0 / Pe, gamma = Gamma gamma0, zeta = Gamma_s
+ * gamma0).  All lengths in the same unit as r_c. */
+typedef struct dpd_params {
+    double L;              /* box side, periodic square; L >= 3 r_c          */
+    int64_t n_beads;       /* N, even, >= 2 (N/2 agents)                     */
+    double a;              /* conservative amplitude A                       */
+    double gamma;          /* pairwise friction gamma >= 0                   */
+    double kBT;            /* k_B T >= 0                                     */
+    double rc;             /* cutoff r_c > 0                                 */
+    double k_bond;         /* spring stiffness kappa >= 0                    */
+    double r0;             /* spring rest length l >= 0                      */
+    double f_p;            /* propulsion per bead f_SP >= 0                  */
+    double zeta;           /* Stokes friction gamma_s >= 0                   */
+    double dt;             /* time step > 0                                  */
+    double mass;           /* bead mass m > 0                                */
+    uint64_t seed;         /* random-stream seed                             */
+    uint32_t replica;      /* XORed into the high key word                   */
+    int32_t exclude_bonded;/* 1 (paper): no pair force inside an agent       */
+    int32_t noise;         /* 0: uniform alpha, 1: Gaussian alpha            */
+    int32_t tile;          /* cell-block side in cells: 0 = default, else
+                              one of 4, 8, 16                                */
+    int32_t variant;       /* pair-kernel variant: 0 = default (fastest),
+                              1 = thread-per-bead, 2 = pair queue            */
+    int32_t reserved;
+} dpd_params;
+
+typedef struct dpd_ctx dpd_ctx;
+
+/* Geometry and counters of a context. */
+typedef struct dpd_info {
+    int64_t n_beads;
+    int32_t n_cells_side;   /* n_c = floor(L / (r_c + 2^-20 L))              */
+    int32_t tile;           /* cell-block side B                             */
+    int32_t n_tiles;        /* ceil(n_c/B)^2                                 */
+    int32_t variant;        /* pair-kernel variant in use                    */
+    int64_t step;           /* current step s of the canonical state         */
+    int64_t overflow_tiles; /* tiles that took the global-memory path since
+                               creation (tile + halo above shared capacity)  */
+    int64_t device_bytes;   /* device memory held by the context             */
+} dpd_info;
+
+/* Status text (static storage). */
+const char *dpd_status_string(int status);
+
+/* Create a context on the current CUDA device, ordered on `stream`.
+ * Validates p (see field comments); allocates all device buffers (about
+ * 100 bytes per bead plus 8 bytes per cell).  The state is undefined until
+ * dpd_set_state or dpd_init_random.  *out receives the context. */
+int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out);
+
+/* Release every resource of ctx; NULL is ignored. */
+void dpd_destroy(dpd_ctx *ctx);
+
+/* Replace the interaction/integration parameters.  n_beads, L and r_c must be
+ * unchanged (DPD_ERR_STATE otherwise: they fix the cell geometry).  Takes
+ * effect at the next step; forces of the current state are not recomputed. */
+int dpd_set_params(dpd_ctx *ctx, const dpd_params *p);
+
+/* Set the canonical state at step `step`.  xv: [N][4] (x, y, vx, vy), id
+ * order, positions anywhere (wrapped into [0, L)).  f: [N][2] forces of that
+ * state, or NULL to compute the set-up force F(x, v, step) (velocities v, the
+ * random stream of `step`).  where: DPD_HOST or DPD_DEVICE for both pointers.
+ * Synchronises the stream. */
+int dpd_set_state(dpd_ctx *ctx, const float *xv, const float *f, int64_t step, int where);
+
+/* Paper's initial condition (Sec. 5): agent centres uniform in the box,
+ * orientations uniform, bond at rest length r0, velocities zero; drawn on the
+ * device from Philox4x32-10 under key (seed, 0x1D17) so it is reproducible;
+ * then the set-up force at step 0. */
+int dpd_init_random(dpd_ctx *ctx, uint64_t seed);
+
+/* Advance n >= 0 velocity-Verlet steps (asynchronous on the stream). */
+int dpd_step(dpd_ctx *ctx, int64_t n);
+
+/* Wait for the stream and return the latched device status. */
+int dpd_sync(dpd_ctx *ctx);
+
+/* Canonical state (x_s, v_s, f_s) and step s.  xv: [N][4], f: [N][2] (may be
+ * NULL), step (may be NULL).  where: DPD_HOST or DPD_DEVICE.  Synchronises. */
+int dpd_get_state(dpd_ctx *ctx, float *xv, float *f, int64_t *step, int where);
+
+/* FP64 reductions over the canonical state of the last completed step:
+ * kinetic energy 1/2 sum m|v|^2, momentum sum m v, temperature
+ * sum m|v|^2 / (2N - 2).  Host outputs.  Synchronise. */
+int dpd_kinetic_energy(dpd_ctx *ctx, double *ke);
+int dpd_momentum(dpd_ctx *ctx, double p[2]);
+int dpd_temperature(dpd_ctx *ctx, double *T);
+
+/* Per-step log of (KE, Px, Py, T) for steps [first, first + count), FP64,
+ * host out [count][4].  The log keeps the last 65536 steps; older ones give
+ * DPD_ERR_INVALID_ARG.  Synchronises. */
+int dpd_thermo_log(dpd_ctx *ctx, int64_t first, int64_t count, double *out);
+
+/* Sec. 5.4 filtered velocity field of the canonical state: agent COM
+ * velocity averaged over a square window of side eps centred on the grid
+ * point (i + 1/2) L/M (minimum image, closed window), 0 where the window is
+ * empty.  eps <= 0 selects eps = L sqrt(10 / N_agents), Eq. (filterwidth).
+ * u: host [M][M][2] (row = y), n_in: host [M][M] window counts or NULL.
+ * 2 <= M <= 1024.  FP64 accumulation.  Synchronises. */
+int dpd_velocity_field(dpd_ctx *ctx, int M, double eps, double *u, double *n_in);
+
+/* Eqs. (fourierTrans01), (ESPf): E(k) = sum over modes with nint|k| = k of
+ * (|uhat_x|^2 + |uhat_y|^2)/2 for k = 1..M/2 of the field above, with
+ * uhat = M^-2 sum u exp(-2 pi i k.x / L).  M a power of two, 4 <= M <= 1024.
+ * E: host [M/2] (E[0] is k = 1).  FP64 FFT on the device.  Synchronises. */
+int dpd_energy_spectrum(dpd_ctx *ctx, int M, double eps, double *E);
+
+/* Eqs. (VCF), (spatial01): all agent pairs with COM separation in
+ * [b dr, (b+1) dr), b < nbins (nbins dr <= L/2 advised):
+ *   g[b] = (<v_a.v_b>_b - |<v>|^2) / (<|v|^2> - |<v>|^2) (global means),
+ * L_int = trapezoid of g over r = 0 (g = 1) and the non-empty bin centres.
+ * Host outputs: g [nbins] (NaN for empty bins or a zero denominator), L_int
+ * (may be NULL), num [nbins] pair sums and cnt [nbins] pair counts (either
+ * may be NULL).  O(N_agents^2) pair pass on the device.  Synchronises. */
+int dpd_velocity_correlation(dpd_ctx *ctx, double dr, int nbins, double *g, double *L_int,
+                             double *num, int64_t *cnt);
+
+/* Debug / parity: per-cell bead counts of the canonical state, row-major
+ * [n_c][n_c] host; and per-bead interacting-neighbour counts (r < r_c,
+ * bonded excluded) in id order, host [N], with the total pair count
+ * (cnt or total may be NULL).  Synchronise. */
+int dpd_cell_counts(dpd_ctx *ctx, uint32_t *counts);
+int dpd_pair_counts(dpd_ctx *ctx, uint32_t *cnt, uint64_t *total);
+
+int dpd_get_info(dpd_ctx *ctx, dpd_info *info);
+
+/* Measurement: advance one step exactly as dpd_step(ctx, 1) does, but with
+ * the three kernels launched one by one between CUDA events on the context's
+ * stream; ms[0..2] receive the device time of the scan, scatter and fused
+ * force/integrate kernels.  Synchronises. */
+int dpd_profile_step(dpd_ctx *ctx, double ms[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPD_H_ */

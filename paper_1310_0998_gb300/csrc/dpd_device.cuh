@@ -1,0 +1,143 @@
+// Device-side building blocks of the DPD dimer simulator (sm_103a).
+//
+// Model: Hinz, Panchenko, Kim & Fried, arXiv:1310.0998, Sec. 2 (forces),
+// Sec. 5 (velocity-Verlet, periodic square).  Random numbers: Philox4x32-10
+// (Salmon et al., SC'11).
+//
+// Data layout in HBM (one system; the ensemble packs several side by side):
+//   S_xv  float4[N]  pre-force state (x, y, v*x, v*y) sorted by cell, where v*
+//                    is the half-step velocity v_{s-1/2} (v_s at set-up)
+//   S_id  u32[N]     bead id of each sorted slot
+//   slot  u32[N]     id -> sorted slot (to find a bead's bonded partner)
+//   U_*             next pre-force state written by the force kernel, in the
+//                    order of S, plus each bead's rank inside its new cell
+//   counts, cstart   cell populations and their exclusive prefix sum
+//   C_xv, C_f        canonical (x_s, v_s), f_s in id order (last step of a call)
+// Cells are numbered tile-major: the domain is cut into B x B cell blocks
+// ("tiles", ragged at the high edge) and the cells of one tile are
+// consecutive, so a tile's own beads form one contiguous run of S.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpd {
+
+enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2, ERR_INTERNAL = 4 };
+enum : int { F_FIRST = 1, F_FINAL = 2, F_ADVANCE = 4 };
+
+constexpr int THERMO_CAP = 65536;   // per-step (KE, Px, Py, -) ring
+constexpr int SCAN_NT = 256;
+constexpr int SCAN_IPT = 16;        // cells per thread in the scan
+constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
+constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (x ~100 ns)
+
+// Per-system view handed to every kernel by value.
+struct Sys {
+    float L, halfL, inv_cs, cs;
+    int nc, ntx, n, ncells;
+    float rc2, inv_rc, a, gamma, sig_r, kbond, r0, fp, zeta, dt, hdtm;
+    uint32_t key0, key1;
+    int noise, excl, cap;
+    float4 *S_xv;
+    uint32_t *S_id;
+    float4 *U_xv;
+    uint32_t *U_id, *U_rank;
+    uint32_t *slot, *counts, *cstart;
+    float4 *C_xv;
+    float2 *C_f;
+    double *thermo;
+    long long *step;
+    uint32_t *pcnt;
+    unsigned long long *ovf;
+    int *err;
+    unsigned long long *scan_status, *scan_ticket;
+};
+
+// ---------------------------------------------------------------- Philox ----
+// One Philox4x32-10 evaluation.  Round: multiply words 0 and 2 by the two
+// round multipliers, mix the high halves with words 1, 3 and the key, keep
+// the low halves; the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ void philox10(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                         uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Random factor of the pair (i, j) at step s: F_R = sig_r * w * noise.
+// Uniform: the odd integer 2 (w0 >> 8) + 1 - 2^24 (|.| < 2^24, exact in FP32);
+// sig_r carries sqrt(2 gamma kBT / dt) * sqrt(3) * 2^-24.
+// Gaussian: Box-Muller on the top 24 bits of w0, w1; sig_r = sqrt(2 gamma kBT / dt).
+__device__ __forceinline__ float pair_noise(const Sys &d, uint32_t ia, uint32_t ib, uint32_t s_lo,
+                                            uint32_t s_hi)
+{
+    uint32_t c0 = min(ia, ib), c1 = max(ia, ib), c2 = s_lo, c3 = s_hi;
+    philox10(c0, c1, c2, c3, d.key0, d.key1);
+    if (d.noise == 0) return (float)((int)((c0 >> 8) * 2u + 1u) - (1 << 24));
+    const float u1 = ((float)(c0 >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    const float u2 = ((float)(c1 >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// ---------------------------------------------------------- cell geometry ----
+// Cell coordinate of an FP32 position in [0, L): min(nc - 1, (int)(x * inv)),
+// inv = (float)nc / (float)L, one IEEE single multiply.
+__device__ __forceinline__ int cell_coord(const Sys &d, float x)
+{
+    const int c = (int)__fmul_rn(x, d.inv_cs);
+    return min(max(c, 0), d.nc - 1);
+}
+
+template <int B>
+__device__ __forceinline__ int cell_of(const Sys &d, int cx, int cy)
+{
+    const int tx = cx / B, lx = cx - tx * B, ty = cy / B, ly = cy - ty * B;
+    const int th = min(B, d.nc - ty * B), tw = min(B, d.nc - tx * B);
+    return ty * B * d.nc + tx * B * th + ly * tw + lx;
+}
+
+// Minimum-image difference a - b of two coordinates in [0, L), formed so that
+// the large operand is shifted by L first (exact) when the pair straddles the
+// periodic boundary.
+__device__ __forceinline__ float minimg(float a, float b, float L, float halfL)
+{
+    float d = a - b;
+    if (d > halfL) d = (a - L) - b;
+    else if (d < -halfL) d = a - (b - L);
+    return d;
+}
+
+// Wrap x + dx back into [0, L) for |dx| < L, keeping precision near 0 and L.
+__device__ __forceinline__ float wrap_add(float x, float dx, float L)
+{
+    float y = x + dx;
+    if (y >= L) y = (x - L) + dx;
+    else if (y < 0.0f) y = y + L;
+    if (y >= L) y -= L;          // y + L rounded up to L
+    if (y < 0.0f) y = 0.0f;
+    return y;
+}
+
+__device__ __forceinline__ void set_err(const Sys &d, int bits) { atomicOr(d.err, bits); }
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+}  // namespace dpd

@@ -1,0 +1,378 @@
+// Observables of Sec. 5.3-5.4 (arXiv:1310.0998) on the device, FP64.
+//
+//   agent COM     c_k = x_tail + 1/2 minimg(x_head - x_tail), wrapped;
+//                 v_k = (v_head + v_tail)/2                       (Sec. 5.3)
+//   u_M           square window of side eps around (i + 1/2) L/M, closed,
+//                 minimum image; mean COM velocity inside, 0 if empty
+//                 (Sec. 5.4, Eq. filterwidth)
+//   E(k)          z = u_x + i u_y, Z = FFT2(z); |uhat_x|^2 + |uhat_y|^2 summed
+//                 over a shell equals |Z|^2 / (2 M^4) summed over the same
+//                 shell, because k -> -k maps each shell onto itself
+//                 (Eqs. fourierTrans01, ESPf)
+//   g_v, L_gv     pair histogram of COM separations, sums of v_a . v_b
+//                 (Eqs. VCF, spatial01)
+// Window and bin decisions use the same IEEE double operations, in the same
+// order, as a plain evaluation of those definitions (explicit _rn intrinsics,
+// no contraction), so they are reproducible bit for bit off the device.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dpd.h"
+#include "sim_host.h"
+
+namespace dpd {
+
+struct ObsScratch {
+    void *buf = nullptr;
+    size_t bytes = 0;
+};
+
+__device__ __forceinline__ double minimg_d(double d, double L)
+{
+    return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+}
+
+__global__ void k_agent_com(const float4 *__restrict__ xv, int na, double L, double2 *c, double2 *v)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const float4 h = xv[2 * k], t = xv[2 * k + 1];
+    const double dx = minimg_d(__dsub_rn((double)h.x, (double)t.x), L);
+    const double dy = minimg_d(__dsub_rn((double)h.y, (double)t.y), L);
+    double cx = __dadd_rn((double)t.x, __dmul_rn(0.5, dx));
+    double cy = __dadd_rn((double)t.y, __dmul_rn(0.5, dy));
+    cx = __dsub_rn(cx, __dmul_rn(L, floor(__ddiv_rn(cx, L))));
+    cy = __dsub_rn(cy, __dmul_rn(L, floor(__ddiv_rn(cy, L))));
+    c[k] = make_double2(cx, cy);
+    v[k] = make_double2(__dmul_rn(0.5, __dadd_rn((double)h.z, (double)t.z)),
+                        __dmul_rn(0.5, __dadd_rn((double)h.w, (double)t.w)));
+}
+
+// Grid indices i whose window [x_i - eps/2, x_i + eps/2] (minimum image)
+// contains coordinate c; at most M of them.
+__device__ __forceinline__ int window_hits(double c, double L, double dxg, double half, int M, int *out, int maxout)
+{
+    const double lo = (c - half) / dxg - 0.5, hi = (c + half) / dxg - 0.5;
+    int i0 = (int)floor(lo) - 1, i1 = (int)ceil(hi) + 1;
+    if (i1 - i0 + 1 > M) { i0 = 0; i1 = M - 1; }
+    int n = 0;
+    for (int ii = i0; ii <= i1 && n < maxout; ++ii) {
+        const int i = ((ii % M) + M) % M;
+        const double xm = __dmul_rn(__dadd_rn((double)i, 0.5), dxg);
+        const double d = minimg_d(__dsub_rn(xm, c), L);
+        if (fabs(d) <= half) out[n++] = i;
+    }
+    return n;
+}
+
+__global__ void k_deposit(const double2 *c, const double2 *v, int na, double L, double dxg, double half, int M,
+                          double *sx, double *sy, double *cnt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    int ix[64], iy[64];
+    const double2 ck = c[k], vk = v[k];
+    const int nx = window_hits(ck.x, L, dxg, half, M, ix, 64);
+    const int ny = window_hits(ck.y, L, dxg, half, M, iy, 64);
+    for (int a = 0; a < ny; ++a)
+        for (int b = 0; b < nx; ++b) {
+            const size_t g = (size_t)iy[a] * M + ix[b];
+            atomicAdd(&sx[g], vk.x);
+            atomicAdd(&sy[g], vk.y);
+            atomicAdd(&cnt[g], 1.0);
+        }
+}
+
+__global__ void k_field_finish(const double *sx, const double *sy, const double *cnt, int MM, double2 *z)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= MM) return;
+    const double n = cnt[g];
+    z[g] = n > 0.0 ? make_double2(sx[g] / n, sy[g] / n) : make_double2(0.0, 0.0);
+}
+
+// In-place radix-2 FFT (forward, e^{-2 pi i k n / M}) of M complex doubles
+// with stride `stride` between elements and `pitch` between transforms; one
+// block per transform, M/2 threads, data staged in shared memory.
+__global__ void k_fft(double2 *z, int M, int logM, int stride, int pitch)
+{
+    extern __shared__ double2 s[];
+    double2 *base = z + (size_t)blockIdx.x * pitch;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const int r = __brev(i) >> (32 - logM);
+        s[r] = base[(size_t)i * stride];
+    }
+    __syncthreads();
+    for (int len = 2; len <= M; len <<= 1) {
+        const int half = len >> 1;
+        for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
+            const int grp = t / half, pos = t - grp * half;
+            const int i0 = grp * len + pos, i1 = i0 + half;
+            double sn, cs;
+            sincospi(-2.0 * (double)pos / (double)len, &sn, &cs);
+            const double2 a = s[i0], b = s[i1];
+            const double2 wb = make_double2(b.x * cs - b.y * sn, b.x * sn + b.y * cs);
+            s[i0] = make_double2(a.x + wb.x, a.y + wb.y);
+            s[i1] = make_double2(a.x - wb.x, a.y - wb.y);
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) base[(size_t)i * stride] = s[i];
+}
+
+__global__ void k_shells(const double2 *Z, int M, double scale, double *E)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M * M) return;
+    const int iy = g / M, ix = g - iy * M;
+    const int ky = iy < M / 2 ? iy : iy - M, kx = ix < M / 2 ? ix : ix - M;
+    const int sh = (int)rint(sqrt((double)(kx * kx + ky * ky)));
+    if (sh >= 1 && sh <= M / 2) {
+        const double2 a = Z[g];
+        atomicAdd(&E[sh - 1], (a.x * a.x + a.y * a.y) * scale);
+    }
+}
+
+__global__ void k_vmeans(const double2 *v, int na, double *acc)
+{
+    double sx = 0, sy = 0, s2 = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < na; k += gridDim.x * blockDim.x) {
+        const double2 a = v[k];
+        sx += a.x;
+        sy += a.y;
+        s2 += a.x * a.x + a.y * a.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], sx);
+        atomicAdd(&acc[1], sy);
+        atomicAdd(&acc[2], s2);
+    }
+}
+
+// All pairs a < b of agents: separation bin floor(r / dr) (IEEE double, as
+// written), accumulate v_a . v_b and the pair count per bin in shared memory.
+constexpr int VCF_TILE = 256;
+__global__ void __launch_bounds__(VCF_TILE) k_vcf(const double2 *c, const double2 *v, int na, double L, double dr,
+                                                  int nbins, double *gnum, unsigned long long *gcnt)
+{
+    extern __shared__ unsigned char smem[];
+    double *snum = (double *)smem;
+    unsigned long long *scnt = (unsigned long long *)(snum + nbins);
+    double2 *sc = (double2 *)(scnt + nbins);
+    double2 *sv = sc + VCF_TILE;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) { snum[b] = 0.0; scnt[b] = 0ull; }
+    const int ntile = (na + VCF_TILE - 1) / VCF_TILE;
+    // block -> (row tile ti, column tile tj >= ti) over the upper triangle
+    // row ti starts at S(ti) = ti*ntile - ti*(ti-1)/2; invert with a square
+    // root and correct by one step either way
+    const long long bid = blockIdx.x, nt = ntile;
+    const double disc = (2.0 * nt + 1.0) * (2.0 * nt + 1.0) - 8.0 * (double)bid;
+    long long ti = (long long)floor(((2.0 * nt + 1.0) - sqrt(fmax(disc, 0.0))) * 0.5);
+    ti = ti < 0 ? 0 : (ti > nt - 1 ? nt - 1 : ti);
+    while (ti > 0 && ti * nt - ti * (ti - 1) / 2 > bid) --ti;
+    while (ti < nt - 1 && (ti + 1) * nt - (ti + 1) * ti / 2 <= bid) ++ti;
+    const int tj = (int)(ti + (bid - (ti * nt - ti * (ti - 1) / 2)));
+    const int a = (int)ti * VCF_TILE + threadIdx.x;
+    const int jb = tj * VCF_TILE;
+    for (int q = threadIdx.x; q < VCF_TILE; q += blockDim.x) {
+        const int j = jb + q;
+        sc[q] = j < na ? c[j] : make_double2(0.0, 0.0);
+        sv[q] = j < na ? v[j] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (a < na) {
+        const double2 ca = c[a], va = v[a];
+        const int jn = min(VCF_TILE, na - jb);
+        for (int q = 0; q < jn; ++q) {
+            const int j = jb + q;
+            if (j <= a) continue;
+            double dx = minimg_d(__dsub_rn(ca.x, sc[q].x), L);
+            double dy = minimg_d(__dsub_rn(ca.y, sc[q].y), L);
+            const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+            const double bf = floor(__ddiv_rn(r, dr));
+            if (bf < (double)nbins) {
+                const int b = (int)bf;
+                atomicAdd(&snum[b], __dadd_rn(__dmul_rn(va.x, sv[q].x), __dmul_rn(va.y, sv[q].y)));
+                atomicAdd(&scnt[b], 1ull);
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        if (scnt[b]) {
+            atomicAdd(&gnum[b], snum[b]);
+            atomicAdd(&gcnt[b], scnt[b]);
+        }
+    }
+}
+
+}  // namespace dpd
+
+using namespace dpd;
+
+static ObsScratch *scratch_of(dpd_ctx *c, size_t bytes)
+{
+    static_assert(sizeof(void *) == 8, "64-bit only");
+    auto *s = reinterpret_cast<ObsScratch *>(c->obs);
+    if (!s) {
+        s = new ObsScratch();
+        c->obs = s;
+    }
+    if (s->bytes < bytes) {
+        if (s->buf) cudaFree(s->buf);
+        s->buf = nullptr;
+        s->bytes = 0;
+        if (cudaMalloc(&s->buf, bytes) != cudaSuccess) return nullptr;
+        s->bytes = bytes;
+    }
+    return s;
+}
+
+void dpd_internal_free_obs(dpd_ctx *c)
+{
+    auto *s = reinterpret_cast<ObsScratch *>(c->obs);
+    if (s) {
+        if (s->buf) cudaFree(s->buf);
+        delete s;
+        c->obs = nullptr;
+    }
+}
+
+#define CUO(x)                                                    \
+    do {                                                          \
+        const cudaError_t e_ = (x);                               \
+        if (e_ != cudaSuccess)                                    \
+            return e_ == cudaErrorMemoryAllocation ? DPD_ERR_OOM : DPD_ERR_CUDA; \
+    } while (0)
+
+// Field on the device: z [M*M] double2 (u_x, u_y), cnt [M*M].
+static int field_device(dpd_ctx *c, int M, double eps, double2 **z_out, double **cnt_out, char **tail)
+{
+    const int na = c->d.n / 2;
+    const size_t MM = (size_t)M * M;
+    const size_t bytes = 16 * (size_t)na * 2 + 8 * MM * 3 + 16 * MM + 8 * 8 + 8 * 65536 * 2 + 1024;
+    ObsScratch *s = scratch_of(c, bytes);
+    if (!s) return DPD_ERR_OOM;
+    char *b = (char *)s->buf;
+    double2 *cc = (double2 *)b; b += 16 * (size_t)na;
+    double2 *vv = (double2 *)b; b += 16 * (size_t)na;
+    double *sx = (double *)b; b += 8 * MM;
+    double *sy = (double *)b; b += 8 * MM;
+    double *cn = (double *)b; b += 8 * MM;
+    double2 *z = (double2 *)b; b += 16 * MM;
+    const double L = c->p.L;
+    if (eps <= 0.0) eps = L * std::sqrt(10.0 / (double)na);
+    CUO(cudaMemsetAsync(sx, 0, 8 * MM * 3, c->st));
+    k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, cc, vv);
+    k_deposit<<<(na + 127) / 128, 128, 0, c->st>>>(cc, vv, na, L, L / M, 0.5 * eps, M, sx, sy, cn);
+    k_field_finish<<<(int)((MM + 255) / 256), 256, 0, c->st>>>(sx, sy, cn, (int)MM, z);
+    CUO(cudaGetLastError());
+    *z_out = z;
+    *cnt_out = cn;
+    if (tail) *tail = b;
+    return DPD_OK;
+}
+
+extern "C" {
+
+int dpd_velocity_field(dpd_ctx *c, int M, double eps, double *u, double *n_in)
+{
+    if (!c || !u || M < 2 || M > 1024) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    if (eps <= 0.0) eps = c->p.L * std::sqrt(10.0 / (double)(c->d.n / 2));
+    if (eps / (c->p.L / M) > 56.0) return DPD_ERR_INVALID_ARG;   // window wider than 56 grid points
+    double2 *z;
+    double *cn;
+    int rc = field_device(c, M, eps, &z, &cn, nullptr);
+    if (rc) return rc;
+    const size_t MM = (size_t)M * M;
+    CUO(cudaMemcpyAsync(u, z, 16 * MM, cudaMemcpyDeviceToHost, c->st));
+    if (n_in) CUO(cudaMemcpyAsync(n_in, cn, 8 * MM, cudaMemcpyDeviceToHost, c->st));
+    return dpd_internal_latched(c);
+}
+
+int dpd_energy_spectrum(dpd_ctx *c, int M, double eps, double *E)
+{
+    if (!c || !E || M < 4 || M > 1024 || (M & (M - 1))) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    if (eps <= 0.0) eps = c->p.L * std::sqrt(10.0 / (double)(c->d.n / 2));
+    if (eps / (c->p.L / M) > 56.0) return DPD_ERR_INVALID_ARG;
+    double2 *z;
+    double *cn;
+    char *tail;
+    int rc = field_device(c, M, eps, &z, &cn, &tail);
+    if (rc) return rc;
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    const size_t sm = 16 * (size_t)M;
+    const int thr = M / 2 < 512 ? M / 2 : 512;
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, 1, M);   // rows (along x)
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, M, 1);   // columns (along y)
+    double *dE = (double *)tail;
+    CUO(cudaMemsetAsync(dE, 0, 8 * (size_t)(M / 2), c->st));
+    const double M2 = (double)M * (double)M;
+    k_shells<<<(M * M + 255) / 256, 256, 0, c->st>>>(z, M, 0.5 / (M2 * M2), dE);
+    CUO(cudaGetLastError());
+    CUO(cudaMemcpyAsync(E, dE, 8 * (size_t)(M / 2), cudaMemcpyDeviceToHost, c->st));
+    return dpd_internal_latched(c);
+}
+
+int dpd_velocity_correlation(dpd_ctx *c, double dr, int nbins, double *g, double *L_int, double *num,
+                             int64_t *cnt)
+{
+    if (!c || !g || !(dr > 0) || nbins < 1 || nbins > 8192) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    const int na = c->d.n / 2;
+    const size_t bytes = 32 * (size_t)na + 16 * (size_t)nbins + 64;
+    ObsScratch *s = scratch_of(c, bytes);
+    if (!s) return DPD_ERR_OOM;
+    char *b = (char *)s->buf;
+    double2 *cc = (double2 *)b; b += 16 * (size_t)na;
+    double2 *vv = (double2 *)b; b += 16 * (size_t)na;
+    double *gnum = (double *)b; b += 8 * (size_t)nbins;
+    unsigned long long *gcnt = (unsigned long long *)b; b += 8 * (size_t)nbins;
+    double *acc = (double *)b;
+    const double L = c->p.L;
+    CUO(cudaMemsetAsync(gnum, 0, 16 * (size_t)nbins + 32, c->st));
+    k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, cc, vv);
+    k_vmeans<<<64, 256, 0, c->st>>>(vv, na, acc);
+    const int ntile = (na + VCF_TILE - 1) / VCF_TILE;
+    const long long nblk = (long long)ntile * (ntile + 1) / 2;
+    const size_t sm = 16 * (size_t)nbins + 32 * VCF_TILE;
+    if (sm > 200 * 1024 || nblk > 2147483647ll) return DPD_ERR_INVALID_ARG;
+    CUO(cudaFuncSetAttribute(k_vcf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_vcf<<<(unsigned)nblk, VCF_TILE, sm, c->st>>>(cc, vv, na, L, dr, nbins, gnum, gcnt);
+    CUO(cudaGetLastError());
+    std::vector<double> hn(nbins), ha(3);
+    std::vector<unsigned long long> hc(nbins);
+    CUO(cudaMemcpyAsync(hn.data(), gnum, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, c->st));
+    CUO(cudaMemcpyAsync(hc.data(), gcnt, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, c->st));
+    CUO(cudaMemcpyAsync(ha.data(), acc, 24, cudaMemcpyDeviceToHost, c->st));
+    const int rc = dpd_internal_latched(c);
+    const double mx = ha[0] / na, my = ha[1] / na, v2 = ha[2] / na, m2 = mx * mx + my * my;
+    const double den = v2 - m2;
+    double li = 0.0, rprev = 0.0, gprev = 1.0;
+    for (int k = 0; k < nbins; ++k) {
+        if (hc[k] > 0 && den > 0) {
+            g[k] = (hn[k] / (double)hc[k] - m2) / den;
+            const double r = (k + 0.5) * dr;
+            li += 0.5 * (g[k] + gprev) * (r - rprev);
+            rprev = r;
+            gprev = g[k];
+        } else {
+            g[k] = NAN;
+        }
+        if (num) num[k] = hn[k];
+        if (cnt) cnt[k] = (int64_t)hc[k];
+    }
+    if (L_int) *L_int = den > 0 ? li : NAN;
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,672 @@
+// Single-system C ABI of the DPD dimer simulator (include/dpd.h).
+//
+// Per step three kernels run on the context's stream, captured once into CUDA
+// graphs (1-step, 8-step and a final step that also writes the canonical
+// state): scan -> scatter -> fused force/integrate (see sim_kernels.cuh).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dpd.h"
+#include "sim_kernels.cuh"
+#include "sim_host.h"
+
+namespace dpd {
+
+// ----------------------------------------------------------------- kernels ----
+__global__ void __launch_bounds__(SCAN_NT) k_scan(Sys d, int nblocks) { scan_decoupled(d, nblocks); }
+
+template <int B>
+__global__ void k_scatter(Sys d)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < d.n) scatter_one<B>(d, k);
+}
+
+template <int B>
+__global__ void k_bin(Sys d)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < d.n) bin_one<B>(d, k);
+}
+
+__global__ void k_iota(Sys d)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < d.n) d.U_id[k] = (uint32_t)k;
+}
+
+__global__ void k_set_step(Sys d, long long s) { *d.step = s; }
+
+// Canonical (x_s, v_s, f_s) in id order -> next pre-force state in U, plus
+// the thermo entry of step s.
+template <int B>
+__global__ void k_kick_bin(Sys d)
+{
+    __shared__ double s_red[3 * 33];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    Thermo3 th{0.f, 0.f, 0.f};
+    if (k < d.n) {
+        float4 xv = d.C_xv[k];
+        const float2 f = d.C_f[k];
+        th.ke = xv.z * xv.z + xv.w * xv.w;
+        th.px = xv.z;
+        th.py = xv.w;
+        float vx = xv.z + d.hdtm * f.x, vy = xv.w + d.hdtm * f.y;
+        float nx = xv.x - d.L * floorf(xv.x / d.L), ny = xv.y - d.L * floorf(xv.y / d.L);
+        if (!(nx >= 0.f && nx < d.L)) nx = 0.f;
+        if (!(ny >= 0.f && ny < d.L)) ny = 0.f;
+        d.C_xv[k] = make_float4(nx, ny, xv.z, xv.w);
+        const float ddx = d.dt * vx, ddy = d.dt * vy;
+        if (isfinite(ddx) && isfinite(ddy) && fabsf(ddx) < d.halfL && fabsf(ddy) < d.halfL) {
+            nx = wrap_add(nx, ddx, d.L);
+            ny = wrap_add(ny, ddy, d.L);
+        } else {
+            set_err(d, ERR_NONFINITE);
+            nx = 0.f; ny = 0.f; vx = 0.f; vy = 0.f;
+        }
+        const int c = cell_of<B>(d, cell_coord(d, nx), cell_coord(d, ny));
+        d.U_rank[k] = atomicAdd(&d.counts[c], 1u);
+        d.U_xv[k] = make_float4(nx, ny, vx, vy);
+        d.U_id[k] = (uint32_t)k;
+    }
+    thermo_flush(d, th, s_red);
+}
+
+template <int B, bool COUNT>
+__global__ void __launch_bounds__(256) k_force(Sys d, int flags)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Thermo3 th{0.f, 0.f, 0.f};
+    force_tile<B, COUNT>(d, blockIdx.x, flags, smem, th);
+    if (flags & (F_ADVANCE | F_FINAL)) {
+        __syncthreads();
+        thermo_flush(d, th, (double *)(smem + TilePlan<B>::red_off()));
+    }
+}
+
+// Paper's initial condition (Sec. 5): per agent k, Philox4x32-10 of counter
+// (k, 0, 0, 0) under key (seed lo, seed hi ^ 0x1D17) gives the centre
+// (u0 L, u1 L) and orientation 2 pi u2; beads at centre +/- r0/2 n; v = 0.
+__global__ void k_init_random(Sys d, unsigned long long seed)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * k + 1 >= d.n) return;
+    uint32_t c0 = (uint32_t)k, c1 = 0, c2 = 0, c3 = 0;
+    philox10(c0, c1, c2, c3, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32) ^ 0x1D17u);
+    const float u0 = (float)(c0 >> 8) * 5.9604644775390625e-08f;
+    const float u1 = (float)(c1 >> 8) * 5.9604644775390625e-08f;
+    const float u2 = (float)(c2 >> 8) * 5.9604644775390625e-08f;
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    const float cx = u0 * d.L, cy = u1 * d.L, h = 0.5f * d.r0;
+    d.U_xv[2 * k] = make_float4(cx + h * cs, cy + h * sn, 0.f, 0.f);
+    d.U_xv[2 * k + 1] = make_float4(cx - h * cs, cy - h * sn, 0.f, 0.f);
+    d.U_id[2 * k] = 2u * k;
+    d.U_id[2 * k + 1] = 2u * k + 1u;
+}
+
+// ------------------------------------------------------------------- host ----
+static int cuerr(cudaError_t e)
+{
+    if (e == cudaSuccess) return DPD_OK;
+    if (e == cudaErrorMemoryAllocation) return DPD_ERR_OOM;
+    return DPD_ERR_CUDA;
+}
+#define CU(x)                                  \
+    do {                                       \
+        const cudaError_t e_ = (x);            \
+        if (e_ != cudaSuccess) return cuerr(e_); \
+    } while (0)
+
+int n_cells_side(double L, double rc) { return (int)std::floor(L / (rc + std::ldexp(1.0, -20) * L)); }
+
+int validate(const dpd_params *p)
+{
+    if (!p) return DPD_ERR_INVALID_ARG;
+    if (!(p->rc > 0) || !(p->L >= 3 * p->rc) || !(p->dt > 0) || !(p->mass > 0)) return DPD_ERR_INVALID_ARG;
+    if (!(p->gamma >= 0) || !(p->zeta >= 0) || !(p->k_bond >= 0) || !(p->kBT >= 0) || !(p->r0 >= 0) ||
+        !(p->f_p >= 0) || !std::isfinite(p->a))
+        return DPD_ERR_INVALID_ARG;
+    if (p->n_beads < 2 || (p->n_beads & 1) || p->n_beads >= (1ll << 31)) return DPD_ERR_INVALID_ARG;
+    if (!(p->tile == 0 || p->tile == 4 || p->tile == 8 || p->tile == 16)) return DPD_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 2) return DPD_ERR_INVALID_ARG;
+    if (p->noise < 0 || p->noise > 1) return DPD_ERR_INVALID_ARG;
+    const int nc = n_cells_side(p->L, p->rc);
+    if (nc < 3 || (double)nc * nc >= 2.0e9) return DPD_ERR_INVALID_ARG;
+    return DPD_OK;
+}
+
+void fill_physics(Sys &d, const dpd_params *p)
+{
+    d.rc2 = (float)(p->rc * p->rc);
+    d.inv_rc = (float)(1.0 / p->rc);
+    d.a = (float)p->a;
+    d.gamma = (float)p->gamma;
+    const double sig = std::sqrt(2.0 * p->gamma * p->kBT / p->dt);
+    d.sig_r = p->noise == 0 ? (float)(sig * std::sqrt(3.0) * std::ldexp(1.0, -24)) : (float)sig;
+    d.kbond = (float)p->k_bond;
+    d.r0 = (float)p->r0;
+    d.fp = (float)p->f_p;
+    d.zeta = (float)p->zeta;
+    d.dt = (float)p->dt;
+    d.hdtm = (float)(0.5 * p->dt / p->mass);
+    d.key0 = (uint32_t)(p->seed & 0xffffffffull);
+    d.key1 = (uint32_t)(p->seed >> 32) ^ p->replica;
+    d.noise = p->noise;
+    d.excl = p->exclude_bonded ? 1 : 0;
+}
+
+void fill_geometry(Sys &d, const dpd_params *p, int B)
+{
+    const int nc = n_cells_side(p->L, p->rc);
+    d.L = (float)p->L;
+    d.halfL = 0.5f * d.L;
+    d.nc = nc;
+    d.inv_cs = (float)nc / d.L;
+    d.cs = d.L / (float)nc;
+    d.ntx = (nc + B - 1) / B;
+    d.n = (int)p->n_beads;
+    d.ncells = nc * nc;
+}
+
+int tile_capacity(const dpd_params *p, int B)
+{
+    const int nc = n_cells_side(p->L, p->rc);
+    const double cs = p->L / nc;
+    const double rho = (double)p->n_beads / (p->L * p->L);
+    const double mean = rho * ((B + 2) * cs) * ((B + 2) * cs);
+    int cap = (int)std::ceil(4.0 * mean + 96.0);
+    cap = (cap + 31) & ~31;
+    return std::max(cap, 256);
+}
+
+size_t force_smem(int B, int cap)
+{
+    switch (B) {
+        case 4: return TilePlan<4>::bytes(cap, 256);
+        case 8: return TilePlan<8>::bytes(cap, 256);
+        default: return TilePlan<16>::bytes(cap, 256);
+    }
+}
+
+template <int B>
+static int set_force_attrs(size_t smem)
+{
+    CU(cudaFuncSetAttribute(k_force<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CU(cudaFuncSetAttribute(k_force<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return DPD_OK;
+}
+
+template <int B>
+static void launch_iteration_t(const Sys &d, cudaStream_t st, int nscan, size_t smem, int flags, bool count)
+{
+    const int ntiles = d.ntx * d.ntx;
+    k_scan<<<nscan, SCAN_NT, 0, st>>>(d, nscan);
+    k_scatter<B><<<(d.n + 255) / 256, 256, 0, st>>>(d);
+    if (count) k_force<B, true><<<ntiles, 256, smem, st>>>(d, flags);
+    else k_force<B, false><<<ntiles, 256, smem, st>>>(d, flags);
+}
+
+void launch_iteration(const Sys &d, int B, cudaStream_t st, int nscan, size_t smem, int flags, bool count)
+{
+    switch (B) {
+        case 4: launch_iteration_t<4>(d, st, nscan, smem, flags, count); break;
+        case 8: launch_iteration_t<8>(d, st, nscan, smem, flags, count); break;
+        default: launch_iteration_t<16>(d, st, nscan, smem, flags, count); break;
+    }
+}
+
+template <int B>
+static void launch_force_only_t(const Sys &d, cudaStream_t st, size_t smem, int flags, bool count)
+{
+    const int ntiles = d.ntx * d.ntx;
+    if (count) k_force<B, true><<<ntiles, 256, smem, st>>>(d, flags);
+    else k_force<B, false><<<ntiles, 256, smem, st>>>(d, flags);
+}
+
+void launch_force_only(const Sys &d, int B, cudaStream_t st, size_t smem, int flags, bool count)
+{
+    switch (B) {
+        case 4: launch_force_only_t<4>(d, st, smem, flags, count); break;
+        case 8: launch_force_only_t<8>(d, st, smem, flags, count); break;
+        default: launch_force_only_t<16>(d, st, smem, flags, count); break;
+    }
+}
+
+void launch_bin(const Sys &d, int B, cudaStream_t st)
+{
+    const int g = (d.n + 255) / 256;
+    switch (B) {
+        case 4: k_bin<4><<<g, 256, 0, st>>>(d); break;
+        case 8: k_bin<8><<<g, 256, 0, st>>>(d); break;
+        default: k_bin<16><<<g, 256, 0, st>>>(d); break;
+    }
+}
+
+void launch_kick_bin(const Sys &d, int B, cudaStream_t st)
+{
+    const int g = (d.n + 255) / 256;
+    switch (B) {
+        case 4: k_kick_bin<4><<<g, 256, 0, st>>>(d); break;
+        case 8: k_kick_bin<8><<<g, 256, 0, st>>>(d); break;
+        default: k_kick_bin<16><<<g, 256, 0, st>>>(d); break;
+    }
+}
+
+int host_cell_of(int B, int nc, int cx, int cy)
+{
+    const int tx = cx / B, lx = cx - tx * B, ty = cy / B, ly = cy - ty * B;
+    const int th = std::min(B, nc - ty * B), tw = std::min(B, nc - tx * B);
+    return ty * B * nc + tx * B * th + ly * tw + lx;
+}
+
+}  // namespace dpd
+
+using namespace dpd;
+
+static void free_graphs(dpd_ctx *c)
+{
+    if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->g8) cudaGraphExecDestroy(c->g8);
+    if (c->gfin) cudaGraphExecDestroy(c->gfin);
+    c->g1 = c->g8 = c->gfin = nullptr;
+}
+
+static int capture(dpd_ctx *c, int iters, int last_flags, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < iters; ++i)
+        launch_iteration(c->d, c->B, c->st, c->nscan, c->smem, i == iters - 1 ? last_flags : F_ADVANCE, false);
+    const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (e != cudaSuccess) return cuerr(e);
+    const cudaError_t e2 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuerr(e2);
+}
+
+static int ensure_graphs(dpd_ctx *c)
+{
+    if (c->g1 && c->g8 && c->gfin) return DPD_OK;
+    free_graphs(c);
+    int rc;
+    if ((rc = capture(c, 1, F_ADVANCE, &c->g1))) return rc;
+    if ((rc = capture(c, 8, F_ADVANCE, &c->g8))) return rc;
+    if ((rc = capture(c, 1, F_ADVANCE | F_FINAL, &c->gfin))) return rc;
+    return DPD_OK;
+}
+
+int dpd_internal_latched(dpd_ctx *c)
+{
+    int e = 0;
+    CU(cudaMemcpyAsync(c->h_pin, c->d.err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    std::memcpy(&e, c->h_pin, sizeof(int));
+    if (e & ERR_NONFINITE) return DPD_ERR_NONFINITE;
+    if (e & ERR_TIMEOUT) return DPD_ERR_TIMEOUT;
+    if (e & ERR_INTERNAL) return DPD_ERR_INTERNAL;
+    return DPD_OK;
+}
+
+extern "C" {
+
+const char *dpd_status_string(int s)
+{
+    switch (s) {
+        case DPD_OK: return "ok";
+        case DPD_ERR_INVALID_ARG: return "invalid argument";
+        case DPD_ERR_CUDA: return "CUDA runtime error";
+        case DPD_ERR_OOM: return "out of device memory";
+        case DPD_ERR_NONFINITE: return "non-finite or runaway state";
+        case DPD_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DPD_ERR_STATE: return "call not valid in this state";
+        case DPD_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
+{
+    if (!out) return DPD_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    dpd_ctx *c = new (std::nothrow) dpd_ctx();
+    if (!c) return DPD_ERR_OOM;
+    c->p = *p;
+    c->B = p->tile ? p->tile : 8;
+    if (stream) {
+        c->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return DPD_ERR_CUDA; }
+        c->own_stream = true;
+    }
+    Sys &d = c->d;
+    fill_geometry(d, p, c->B);
+    fill_physics(d, p);
+    d.cap = tile_capacity(p, c->B);
+    c->smem = force_smem(c->B, d.cap);
+    if (c->smem > 200 * 1024) {
+        d.cap = (int)((200 * 1024 - force_smem(c->B, 0)) / 33) & ~31;
+        c->smem = force_smem(c->B, d.cap);
+    }
+    c->nscan = (d.ncells + SCAN_TILE - 1) / SCAN_TILE;
+    const size_t n = (size_t)d.n, nce = (size_t)d.ncells;
+    // one pool, 256-byte aligned slices
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_S = take(16 * n), o_Sid = take(4 * n), o_U = take(16 * n), o_Uid = take(4 * n),
+                 o_Ur = take(4 * n), o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
+                 o_C = take(16 * n), o_Cf = take(8 * n), o_th = take(sizeof(double) * 4 * THERMO_CAP),
+                 o_step = take(8), o_pc = take(4 * n), o_ovf = take(8), o_err = take(8),
+                 o_ss = take(8 * (size_t)c->nscan), o_tk = take(8);
+    c->pool_bytes = off;
+    if (cudaMalloc(&c->pool, off) != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->st);
+        delete c;
+        return DPD_ERR_OOM;
+    }
+    if (cudaMallocHost((void **)&c->h_pin, 4096) != cudaSuccess) {
+        cudaFree(c->pool);
+        if (c->own_stream) cudaStreamDestroy(c->st);
+        delete c;
+        return DPD_ERR_OOM;
+    }
+    char *b = (char *)c->pool;
+    d.S_xv = (float4 *)(b + o_S);
+    d.S_id = (uint32_t *)(b + o_Sid);
+    d.U_xv = (float4 *)(b + o_U);
+    d.U_id = (uint32_t *)(b + o_Uid);
+    d.U_rank = (uint32_t *)(b + o_Ur);
+    d.slot = (uint32_t *)(b + o_slot);
+    d.counts = (uint32_t *)(b + o_cnt);
+    d.cstart = (uint32_t *)(b + o_cst);
+    d.C_xv = (float4 *)(b + o_C);
+    d.C_f = (float2 *)(b + o_Cf);
+    d.thermo = (double *)(b + o_th);
+    d.step = (long long *)(b + o_step);
+    d.pcnt = nullptr;
+    c->pcnt_buf = (uint32_t *)(b + o_pc);
+    d.ovf = (unsigned long long *)(b + o_ovf);
+    d.err = (int *)(b + o_err);
+    d.scan_status = (unsigned long long *)(b + o_ss);
+    d.scan_ticket = (unsigned long long *)(b + o_tk);
+    if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess ||
+        (rc = (c->B == 4 ? set_force_attrs<4>(c->smem) : c->B == 8 ? set_force_attrs<8>(c->smem)
+                                                              : set_force_attrs<16>(c->smem))) != DPD_OK) {
+        dpd_destroy(c);
+        return rc ? rc : DPD_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) { dpd_destroy(c); return DPD_ERR_CUDA; }
+    *out = c;
+    return DPD_OK;
+}
+
+void dpd_destroy(dpd_ctx *c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    free_graphs(c);
+    dpd_internal_free_obs(c);
+    if (c->pool) cudaFree(c->pool);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+int dpd_set_params(dpd_ctx *c, const dpd_params *p)
+{
+    if (!c) return DPD_ERR_INVALID_ARG;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (p->n_beads != c->p.n_beads || p->L != c->p.L || p->rc != c->p.rc) return DPD_ERR_STATE;
+    const int B = p->tile ? p->tile : 8;
+    if (B != c->B) return DPD_ERR_STATE;
+    c->p = *p;
+    fill_physics(c->d, p);
+    free_graphs(c);   // kernel arguments carry the parameters
+    return DPD_OK;
+}
+
+static int start_from_U(dpd_ctx *c, long long step)
+{
+    // U holds an unbinned state in id order: bin it, then the set-up step.
+    launch_bin(c->d, c->B, c->st);
+    k_set_step<<<1, 1, 0, c->st>>>(c->d, step - 1);
+    launch_iteration(c->d, c->B, c->st, c->nscan, c->smem, F_FIRST | F_FINAL | F_ADVANCE, false);
+    CU(cudaGetLastError());
+    c->step = step;
+    c->have_state = true;
+    c->sorted_canonical = true;
+    return dpd_internal_latched(c);
+}
+
+int dpd_set_state(dpd_ctx *c, const float *xv, const float *f, int64_t step, int where)
+{
+    if (!c || !xv || (where != DPD_HOST && where != DPD_DEVICE)) return DPD_ERR_INVALID_ARG;
+    const size_t n = (size_t)c->d.n;
+    const cudaMemcpyKind kind = where == DPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CU(cudaMemsetAsync(c->d.err, 0, sizeof(int), c->st));
+    CU(cudaMemsetAsync(c->d.counts, 0, sizeof(uint32_t) * (size_t)c->d.ncells, c->st));
+    if (!f) {
+        CU(cudaMemcpyAsync(c->d.U_xv, xv, 16 * n, kind, c->st));
+        k_iota<<<(c->d.n + 255) / 256, 256, 0, c->st>>>(c->d);
+        return start_from_U(c, step);
+    }
+    CU(cudaMemcpyAsync(c->d.C_xv, xv, 16 * n, kind, c->st));
+    CU(cudaMemcpyAsync(c->d.C_f, f, 8 * n, kind, c->st));
+    k_set_step<<<1, 1, 0, c->st>>>(c->d, step);
+    CU(cudaMemsetAsync(c->d.thermo + 4 * (size_t)(step % THERMO_CAP), 0, 4 * sizeof(double), c->st));
+    launch_kick_bin(c->d, c->B, c->st);
+    CU(cudaGetLastError());
+    c->step = step;
+    c->have_state = true;
+    c->sorted_canonical = false;
+    return dpd_internal_latched(c);
+}
+
+int dpd_init_random(dpd_ctx *c, uint64_t seed)
+{
+    if (!c) return DPD_ERR_INVALID_ARG;
+    CU(cudaMemsetAsync(c->d.err, 0, sizeof(int), c->st));
+    CU(cudaMemsetAsync(c->d.counts, 0, sizeof(uint32_t) * (size_t)c->d.ncells, c->st));
+    k_init_random<<<(c->d.n / 2 + 255) / 256, 256, 0, c->st>>>(c->d, (unsigned long long)seed);
+    return start_from_U(c, 0);
+}
+
+int dpd_step(dpd_ctx *c, int64_t n)
+{
+    if (!c || n < 0) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    if (n == 0) return DPD_OK;
+    int rc = ensure_graphs(c);
+    if (rc) return rc;
+    const int64_t body = n - 1;
+    for (int64_t i = 0; i < body / 8; ++i) CU(cudaGraphLaunch(c->g8, c->st));
+    for (int64_t i = 0; i < body % 8; ++i) CU(cudaGraphLaunch(c->g1, c->st));
+    CU(cudaGraphLaunch(c->gfin, c->st));
+    c->step += n;
+    c->sorted_canonical = true;
+    return DPD_OK;
+}
+
+int dpd_sync(dpd_ctx *c)
+{
+    if (!c) return DPD_ERR_INVALID_ARG;
+    return dpd_internal_latched(c);
+}
+
+int dpd_get_state(dpd_ctx *c, float *xv, float *f, int64_t *step, int where)
+{
+    if (!c || (where != DPD_HOST && where != DPD_DEVICE)) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    const size_t n = (size_t)c->d.n;
+    const cudaMemcpyKind kind = where == DPD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (xv) CU(cudaMemcpyAsync(xv, c->d.C_xv, 16 * n, kind, c->st));
+    if (f) CU(cudaMemcpyAsync(f, c->d.C_f, 8 * n, kind, c->st));
+    if (step) *step = c->step;
+    return dpd_internal_latched(c);
+}
+
+static int thermo_entry(dpd_ctx *c, long long s, double out[4])
+{
+    CU(cudaMemcpyAsync(c->h_pin, c->d.thermo + 4 * (size_t)(s % THERMO_CAP), 4 * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->st));
+    int rc = dpd_internal_latched(c);
+    const double m = c->p.mass, n = (double)c->d.n;
+    out[0] = 0.5 * m * c->h_pin[0];
+    out[1] = m * c->h_pin[1];
+    out[2] = m * c->h_pin[2];
+    out[3] = m * c->h_pin[0] / (2.0 * n - 2.0);
+    return rc;
+}
+
+int dpd_kinetic_energy(dpd_ctx *c, double *ke)
+{
+    if (!c || !ke) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    double t[4];
+    const int rc = thermo_entry(c, c->step, t);
+    *ke = t[0];
+    return rc;
+}
+
+int dpd_momentum(dpd_ctx *c, double p[2])
+{
+    if (!c || !p) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    double t[4];
+    const int rc = thermo_entry(c, c->step, t);
+    p[0] = t[1];
+    p[1] = t[2];
+    return rc;
+}
+
+int dpd_temperature(dpd_ctx *c, double *T)
+{
+    if (!c || !T) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    double t[4];
+    const int rc = thermo_entry(c, c->step, t);
+    *T = t[3];
+    return rc;
+}
+
+int dpd_thermo_log(dpd_ctx *c, int64_t first, int64_t count, double *out)
+{
+    if (!c || !out || count < 0) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    if (count == 0) return DPD_OK;
+    if (first + count - 1 > c->step || first <= c->step - THERMO_CAP || count > THERMO_CAP)
+        return DPD_ERR_INVALID_ARG;
+    std::vector<double> raw(4 * (size_t)count);
+    int64_t done = 0;
+    while (done < count) {
+        const int64_t s = first + done;
+        const int64_t slot = s % THERMO_CAP;
+        const int64_t run = std::min<int64_t>(count - done, THERMO_CAP - slot);
+        CU(cudaMemcpyAsync(raw.data() + 4 * done, c->d.thermo + 4 * slot, 4 * sizeof(double) * run,
+                           cudaMemcpyDeviceToHost, c->st));
+        done += run;
+    }
+    const int rc = dpd_internal_latched(c);
+    const double m = c->p.mass, n = (double)c->d.n;
+    for (int64_t k = 0; k < count; ++k) {
+        out[4 * k + 0] = 0.5 * m * raw[4 * k];
+        out[4 * k + 1] = m * raw[4 * k + 1];
+        out[4 * k + 2] = m * raw[4 * k + 2];
+        out[4 * k + 3] = m * raw[4 * k] / (2.0 * n - 2.0);
+    }
+    return rc;
+}
+
+int dpd_cell_counts(dpd_ctx *c, uint32_t *counts)
+{
+    if (!c || !counts) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state || !c->sorted_canonical) return DPD_ERR_STATE;
+    const int nc = c->d.nc;
+    std::vector<uint32_t> cs((size_t)c->d.ncells + 1);
+    CU(cudaMemcpyAsync(cs.data(), c->d.cstart, 4 * cs.size(), cudaMemcpyDeviceToHost, c->st));
+    const int rc = dpd_internal_latched(c);
+    for (int cy = 0; cy < nc; ++cy)
+        for (int cx = 0; cx < nc; ++cx) {
+            const int g = host_cell_of(c->B, nc, cx, cy);
+            counts[(size_t)cy * nc + cx] = cs[g + 1] - cs[g];
+        }
+    return rc;
+}
+
+int dpd_pair_counts(dpd_ctx *c, uint32_t *cnt, uint64_t *total)
+{
+    if (!c) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state || !c->sorted_canonical) return DPD_ERR_STATE;
+    const size_t n = (size_t)c->d.n;
+    Sys d = c->d;
+    d.pcnt = c->pcnt_buf;
+    launch_force_only(d, c->B, c->st, c->smem, 0, true);
+    CU(cudaGetLastError());
+    std::vector<uint32_t> h(n);
+    CU(cudaMemcpyAsync(h.data(), c->pcnt_buf, 4 * n, cudaMemcpyDeviceToHost, c->st));
+    const int rc = dpd_internal_latched(c);
+    uint64_t t = 0;
+    for (size_t i = 0; i < n; ++i) t += h[i];
+    if (cnt) std::memcpy(cnt, h.data(), 4 * n);
+    if (total) *total = t / 2;
+    return rc;
+}
+
+int dpd_profile_step(dpd_ctx *c, double ms[3])
+{
+    if (!c || !ms) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    cudaEvent_t ev[4];
+    for (int i = 0; i < 4; ++i) CU(cudaEventCreate(&ev[i]));
+    const Sys &d = c->d;
+    CU(cudaEventRecord(ev[0], c->st));
+    k_scan<<<c->nscan, SCAN_NT, 0, c->st>>>(d, c->nscan);
+    CU(cudaEventRecord(ev[1], c->st));
+    switch (c->B) {
+        case 4: k_scatter<4><<<(d.n + 255) / 256, 256, 0, c->st>>>(d); break;
+        case 8: k_scatter<8><<<(d.n + 255) / 256, 256, 0, c->st>>>(d); break;
+        default: k_scatter<16><<<(d.n + 255) / 256, 256, 0, c->st>>>(d); break;
+    }
+    CU(cudaEventRecord(ev[2], c->st));
+    launch_force_only(d, c->B, c->st, c->smem, F_ADVANCE | F_FINAL, false);
+    CU(cudaEventRecord(ev[3], c->st));
+    CU(cudaGetLastError());
+    c->step += 1;
+    c->sorted_canonical = true;
+    const int rc = dpd_internal_latched(c);
+    for (int i = 0; i < 3; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        ms[i] = t;
+    }
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+int dpd_get_info(dpd_ctx *c, dpd_info *info)
+{
+    if (!c || !info) return DPD_ERR_INVALID_ARG;
+    unsigned long long ovf = 0;
+    CU(cudaMemcpyAsync(c->h_pin, c->d.ovf, 8, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    std::memcpy(&ovf, c->h_pin, 8);
+    info->n_beads = c->d.n;
+    info->n_cells_side = c->d.nc;
+    info->tile = c->B;
+    info->n_tiles = c->d.ntx * c->d.ntx;
+    info->variant = 1;
+    info->step = c->step;
+    info->overflow_tiles = (int64_t)ovf;
+    info->device_bytes = (int64_t)c->pool_bytes;
+    return DPD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,496 @@
+// Per-step device work of the DPD dimer simulator, written as device
+// functions so that the single-system kernels and the persistent ensemble
+// kernel share them.
+//
+// One step s -> s+1 (standard velocity-Verlet, Sec. 5 of arXiv:1310.0998):
+//   scan     cstart = exclusive_scan(counts), counts = 0, step += 1
+//   scatter  U (unsorted, with ranks) -> S sorted by cell, slot[id]
+//   force    per tile: pair forces (Eqs. DPDf, DPDcdr, weightFunc01), bond
+//            (Eq. stiffSpring), propulsion and drag (Eq. DPDnp); then
+//            v_s = v* + dt/2m f_s (skipped at set-up), FP64 thermo partials,
+//            v_{s+1/2} = v_s + dt/2m f_s, x_{s+1} = wrap(x_s + dt v_{s+1/2}),
+//            binning of x_{s+1} into counts (rank = atomic ticket) -> U.
+#pragma once
+#include "dpd_device.cuh"
+
+namespace dpd {
+
+// ------------------------------------------------------------------ scan ----
+// Single-pass exclusive scan with decoupled look-back over blocks of
+// SCAN_TILE cells.  Logical block ids come from a monotonically growing
+// ticket so predecessors always run first; the epoch (ticket / nblocks) tags
+// the status words so nothing needs clearing between launches.  Waits are
+// bounded: on timeout the error bit is set and the scan continues.
+__device__ void scan_decoupled(const Sys &d, int nblocks)
+{
+    __shared__ uint32_t s_warp[SCAN_NT / 32];
+    __shared__ uint32_t s_excl;
+    __shared__ int s_bid;
+    __shared__ uint32_t s_epoch;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const unsigned long long t = atomicAdd(d.scan_ticket, 1ull);
+        s_bid = (int)(t % (unsigned long long)nblocks);
+        s_epoch = (uint32_t)((t / (unsigned long long)nblocks + 1ull) & 0x3fffffffull);
+    }
+    __syncthreads();
+    const int bid = s_bid;
+    const unsigned long long ep = s_epoch;
+    const int base = bid * SCAN_TILE + tid * SCAN_IPT;
+    uint32_t v[SCAN_IPT];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+        const int idx = base + k;
+        v[k] = idx < d.ncells ? d.counts[idx] : 0u;
+        sum += v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+        const int idx = base + k;
+        if (idx < d.ncells) d.counts[idx] = 0u;
+    }
+    // block exclusive scan of the per-thread sums
+    const int lane = tid & 31, wid = tid >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < SCAN_NT / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < SCAN_NT / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+        if (lane == SCAN_NT / 32 - 1) {
+            const uint32_t total = wi;
+            uint32_t excl = 0;
+            unsigned long long *st = d.scan_status;
+            if (bid == 0) {
+                st_release_u64(&st[0], (ep << 34) | (2ull << 32) | total);
+            } else {
+                st_release_u64(&st[bid], (ep << 34) | (1ull << 32) | total);
+                int j = bid - 1;
+                long long spins = 0;
+                while (j >= 0) {
+                    const unsigned long long w64 = ld_acquire_u64(&st[j]);
+                    const unsigned long long wep = w64 >> 34, fl = (w64 >> 32) & 3ull;
+                    if (wep != ep || fl == 0ull) {
+                        if (++spins > SPIN_LIMIT) { set_err(d, ERR_TIMEOUT); break; }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    excl += (uint32_t)w64;
+                    if (fl == 2ull) break;
+                    --j;
+                }
+                st_release_u64(&st[bid], (ep << 34) | (2ull << 32) | (excl + total));
+            }
+            s_excl = excl;
+            if (bid == nblocks - 1) d.cstart[d.ncells] = excl + total;
+        }
+    }
+    __syncthreads();
+    uint32_t run = s_excl + s_warp[wid] + (incl - sum);
+#pragma unroll
+    for (int k = 0; k < SCAN_IPT; ++k) {
+        const int idx = base + k;
+        if (idx < d.ncells) d.cstart[idx] = run;
+        run += v[k];
+    }
+    if (bid == 0 && tid == 0) {
+        const long long s1 = *d.step + 1;
+        *d.step = s1;
+        double *th = d.thermo + 4 * (size_t)(s1 % THERMO_CAP);
+        th[0] = 0.0; th[1] = 0.0; th[2] = 0.0; th[3] = 0.0;
+    }
+}
+
+// --------------------------------------------------------------- scatter ----
+template <int B>
+__device__ __forceinline__ void scatter_one(const Sys &d, int k)
+{
+    const float4 xv = d.U_xv[k];
+    const uint32_t id = d.U_id[k], rank = d.U_rank[k];
+    const int c = cell_of<B>(d, cell_coord(d, xv.x), cell_coord(d, xv.y));
+    const uint32_t dst = d.cstart[c] + rank;
+    if (dst >= (uint32_t)d.n || id >= (uint32_t)d.n) { set_err(d, ERR_INTERNAL); return; }
+    d.S_xv[dst] = xv;
+    d.S_id[dst] = id;
+    d.slot[id] = dst;
+}
+
+// Bin an uploaded/initial state held in U (wrap, check, rank).
+template <int B>
+__device__ __forceinline__ void bin_one(const Sys &d, int k)
+{
+    float4 xv = d.U_xv[k];
+    if (!(isfinite(xv.x) && isfinite(xv.y) && isfinite(xv.z) && isfinite(xv.w))) {
+        set_err(d, ERR_NONFINITE);
+        xv = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    xv.x = xv.x - d.L * floorf(xv.x / d.L);
+    xv.y = xv.y - d.L * floorf(xv.y / d.L);
+    if (!(xv.x >= 0.f && xv.x < d.L)) xv.x = 0.f;
+    if (!(xv.y >= 0.f && xv.y < d.L)) xv.y = 0.f;
+    d.U_xv[k] = xv;
+    const int c = cell_of<B>(d, cell_coord(d, xv.x), cell_coord(d, xv.y));
+    d.U_rank[k] = atomicAdd(&d.counts[c], 1u);
+}
+
+// ------------------------------------------------------------- integrate ----
+struct Thermo3 { float ke, px, py; };
+
+// Everything after the pair sum for one owned bead at sorted slot g:
+// bond + propulsion (partner through slot[id ^ 1]), drag, the two half kicks
+// and the drift, canonical output, binning of the new position.
+template <int B>
+__device__ __forceinline__ void integrate_bead(const Sys &d, int g, float4 xv, uint32_t id, float fx,
+                                               float fy, int flags, Thermo3 &th)
+{
+    const uint32_t ps = d.slot[id ^ 1u];
+    if (ps < (uint32_t)d.n) {
+        const float4 xp = d.S_xv[ps];
+        const float dx = minimg(xv.x, xp.x, d.L, d.halfL);
+        const float dy = minimg(xv.y, xp.y, d.L, d.halfL);
+        const float r2 = dx * dx + dy * dy;
+        if (r2 > 0.f) {
+            const float r = sqrtf(r2);
+            const float inv = 1.0f / r;
+            const float ex = dx * inv, ey = dy * inv;   // from partner to self
+            const float fb = -d.kbond * (r - d.r0);
+            const float sp = (id & 1u) ? -d.fp : d.fp;  // n_k = head - tail
+            fx += (fb + sp) * ex;
+            fy += (fb + sp) * ey;
+        }
+    } else {
+        set_err(d, ERR_INTERNAL);
+    }
+    fx -= d.zeta * xv.z;
+    fy -= d.zeta * xv.w;
+    float vx = xv.z, vy = xv.w;
+    if (!(flags & F_FIRST)) { vx += d.hdtm * fx; vy += d.hdtm * fy; }
+    th.ke += vx * vx + vy * vy;
+    th.px += vx;
+    th.py += vy;
+    if (flags & F_FINAL) {
+        d.C_xv[id] = make_float4(xv.x, xv.y, vx, vy);
+        d.C_f[id] = make_float2(fx, fy);
+    }
+    if (flags & F_ADVANCE) {
+        vx += d.hdtm * fx;
+        vy += d.hdtm * fy;
+        const float ddx = d.dt * vx, ddy = d.dt * vy;
+        float nx, ny;
+        if (isfinite(ddx) && isfinite(ddy) && fabsf(ddx) < d.halfL && fabsf(ddy) < d.halfL) {
+            nx = wrap_add(xv.x, ddx, d.L);
+            ny = wrap_add(xv.y, ddy, d.L);
+        } else {
+            set_err(d, ERR_NONFINITE);
+            nx = 0.f; ny = 0.f; vx = 0.f; vy = 0.f;
+        }
+        const int c = cell_of<B>(d, cell_coord(d, nx), cell_coord(d, ny));
+        d.U_rank[g] = atomicAdd(&d.counts[c], 1u);
+        d.U_xv[g] = make_float4(nx, ny, vx, vy);
+        d.U_id[g] = id;
+    }
+}
+
+
+// ------------------------------------------------------------ force tile ----
+// Shared-memory plan of one tile (B x B owned cells + one-cell halo).
+template <int B>
+struct TilePlan {
+    static constexpr int NCL = (B + 2) * (B + 2);   // local cell table
+    static constexpr int NH = 4 * B + 4;            // halo cells
+    static constexpr int NINT = 2 * NCL + 5 * (NH + 1) + 8;
+    static __host__ __device__ size_t red_off() { return ((size_t)NINT * 4 + 7) & ~size_t(7); }
+    static __host__ __device__ size_t bead_off(int nthreads)
+    {
+        return (red_off() + sizeof(double) * 3 * (size_t)(nthreads / 32 + 1) + 15) & ~size_t(15);
+    }
+    static __host__ __device__ size_t bytes(int cap, int nthreads)
+    {
+        return (bead_off(nthreads) + (size_t)cap * (8 + 8 + 4 + 4 + 4 + 4 + 1) + 15) & ~size_t(15);
+    }
+};
+
+__device__ __forceinline__ float dpd_pair_scalar(const Sys &d, float dx, float dy, float dvx, float dvy,
+                                                 uint32_t idi, uint32_t idj, uint32_t s_lo, uint32_t s_hi,
+                                                 float r2, float &ex, float &ey)
+{
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float w = 1.0f - r * d.inv_rc;
+    ex = dx * rinv;
+    ey = dy * rinv;
+    const float dve = dvx * ex + dvy * ey;
+    const float nz = pair_noise(d, idi, idj, s_lo, s_hi);
+    return w * (d.a - d.gamma * w * dve + d.sig_r * nz);
+}
+
+// Fused force + integrate for one tile.  Thread-per-owned-bead pair search:
+// pairs inside the tile are taken once (Newton-3 through shared-memory
+// atomics on the partner's slot), pairs with halo beads are taken from the
+// owned side only (the neighbouring tile takes the other side with the same
+// random number), so every bead's force is complete when the tile finishes
+// and the integration runs in the same kernel.  A tile whose beads do not
+// fit in shared memory takes the same arithmetic from global memory.
+template <int B, bool COUNT>
+__device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *smem, Thermo3 &th)
+{
+    using TP = TilePlan<B>;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    int *s_cbeg = (int *)smem;
+    int *s_ccnt = s_cbeg + TP::NCL;
+    int *s_hg = s_ccnt + TP::NCL;
+    int *s_hbeg = s_hg + (TP::NH + 1);
+    int *s_hcnt = s_hbeg + (TP::NH + 1);
+    int *s_hsx = s_hcnt + (TP::NH + 1);
+    int *s_hsy = s_hsx + (TP::NH + 1);
+    int *s_sc = s_hsy + (TP::NH + 1);
+    const int cap = d.cap;
+    float2 *s_pos = (float2 *)(smem + TP::bead_off(NT));
+    float2 *s_vel = s_pos + cap;
+    uint32_t *s_id = (uint32_t *)(s_vel + cap);
+    float *s_fx = (float *)(s_id + cap);
+    float *s_fy = s_fx + cap;
+    uint32_t *s_cnt = (uint32_t *)(s_fy + cap);
+    unsigned char *s_lc = (unsigned char *)(s_cnt + cap);
+
+    const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
+    const int x0 = tx * B, y0 = ty * B;
+    const int tw = min(B, d.nc - x0), th_ = min(B, d.nc - y0);
+    const int base = y0 * d.nc + x0 * th_;
+    const int nh = 2 * (tw + 2) + 2 * th_;
+    const float ox = ((float)x0 + 0.5f * (float)tw) * d.cs;
+    const float oy = ((float)y0 + 0.5f * (float)th_) * d.cs;
+    const float oxL = ox - d.L, oyL = oy - d.L;
+    const uint32_t n = (uint32_t)d.n;
+    const long long step = *d.step;
+    const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
+    const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+
+    const uint32_t g0 = min(d.cstart[base], n);
+    const uint32_t g1 = max(g0, min(d.cstart[base + tw * th_], n));
+    const int n_own = (int)(g1 - g0);
+
+    // owned cell table
+    for (int c = tid; c < tw * th_; c += NT) {
+        const int ly = c / tw, lx = c - ly * tw;
+        const uint32_t b = min(max(d.cstart[base + c], g0), g1), e = min(max(d.cstart[base + c + 1], b), g1);
+        const int lc = (ly + 1) * (B + 2) + lx + 1;
+        s_cbeg[lc] = (int)(b - g0);
+        s_ccnt[lc] = (int)(e - b);
+    }
+    // halo cell table
+    for (int h = tid; h < nh; h += NT) {
+        int lx, ly;
+        if (h < tw + 2) { lx = h - 1; ly = -1; }
+        else if (h < 2 * (tw + 2)) { lx = h - (tw + 2) - 1; ly = th_; }
+        else if (h < 2 * (tw + 2) + th_) { lx = -1; ly = h - 2 * (tw + 2); }
+        else { lx = tw; ly = h - 2 * (tw + 2) - th_; }
+        int cx = x0 + lx, cy = y0 + ly, sx = 0, sy = 0;
+        if (cx < 0) { cx += d.nc; sx = -1; } else if (cx >= d.nc) { cx -= d.nc; sx = 1; }
+        if (cy < 0) { cy += d.nc; sy = -1; } else if (cy >= d.nc) { cy -= d.nc; sy = 1; }
+        const int gc = cell_of<B>(d, cx, cy);
+        const uint32_t b = min(d.cstart[gc], n), e = min(max(d.cstart[gc + 1], b), n);
+        s_hg[h] = (int)b;
+        s_hcnt[h] = (int)(e - b);
+        s_hsx[h] = sx;
+        s_hsy[h] = sy;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int run = n_own;
+        for (int h = 0; h < nh; ++h) {
+            int lx, ly;
+            if (h < tw + 2) { lx = h - 1; ly = -1; }
+            else if (h < 2 * (tw + 2)) { lx = h - (tw + 2) - 1; ly = th_; }
+            else if (h < 2 * (tw + 2) + th_) { lx = -1; ly = h - 2 * (tw + 2); }
+            else { lx = tw; ly = h - 2 * (tw + 2) - th_; }
+            const int lc = (ly + 1) * (B + 2) + lx + 1;
+            s_hbeg[h] = run;
+            s_cbeg[lc] = run;
+            s_ccnt[lc] = s_hcnt[h];
+            run += s_hcnt[h];
+        }
+        s_hbeg[nh] = run;
+        s_sc[0] = run;
+    }
+    __syncthreads();
+    const int total = s_sc[0];
+
+    if (total <= cap) {
+        // ---- stage owned + halo beads in shared memory (tile-local frame)
+        for (int k = tid; k < n_own; k += NT) {
+            const float4 xv = d.S_xv[g0 + k];
+            s_pos[k] = make_float2(xv.x - ox, xv.y - oy);
+            s_vel[k] = make_float2(xv.z, xv.w);
+            s_id[k] = d.S_id[g0 + k];
+            s_fx[k] = 0.f;
+            s_fy[k] = 0.f;
+            if (COUNT) s_cnt[k] = 0u;
+            const int lx = min(max(cell_coord(d, xv.x) - x0, 0), tw - 1);
+            const int ly = min(max(cell_coord(d, xv.y) - y0, 0), th_ - 1);
+            s_lc[k] = (unsigned char)(lx | (ly << 4));
+        }
+        for (int k = n_own + tid; k < total; k += NT) {
+            int lo = 0, hi = nh - 1;   // last h with hbeg[h] <= k
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_hbeg[mid] <= k) lo = mid; else hi = mid - 1;
+            }
+            const int h = lo;
+            const uint32_t gsrc = (uint32_t)s_hg[h] + (uint32_t)(k - s_hbeg[h]);
+            const float4 xv = d.S_xv[min(gsrc, n - 1)];
+            const float px = s_hsx[h] < 0 ? (xv.x - d.L) - ox : (s_hsx[h] > 0 ? xv.x - oxL : xv.x - ox);
+            const float py = s_hsy[h] < 0 ? (xv.y - d.L) - oy : (s_hsy[h] > 0 ? xv.y - oyL : xv.y - oy);
+            s_pos[k] = make_float2(px, py);
+            s_vel[k] = make_float2(xv.z, xv.w);
+            s_id[k] = d.S_id[min(gsrc, n - 1)];
+        }
+        __syncthreads();
+
+        // ---- pair forces
+        for (int k = tid; k < n_own; k += NT) {
+            const float2 pi = s_pos[k], vi = s_vel[k];
+            const uint32_t idi = s_id[k], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
+            const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
+            float fx = 0.f, fy = 0.f;
+            uint32_t cnt = 0;
+#pragma unroll 1
+            for (int nb = 0; nb < 9; ++nb) {
+                int ox_ = 0, oy_ = 0;
+                switch (nb) {
+                    case 1: ox_ = 1; oy_ = 0; break;
+                    case 2: ox_ = 1; oy_ = 1; break;
+                    case 3: ox_ = 0; oy_ = 1; break;
+                    case 4: ox_ = -1; oy_ = 1; break;
+                    case 5: ox_ = -1; oy_ = 0; break;
+                    case 6: ox_ = -1; oy_ = -1; break;
+                    case 7: ox_ = 0; oy_ = -1; break;
+                    case 8: ox_ = 1; oy_ = -1; break;
+                    default: break;
+                }
+                const int nlx = lx + ox_, nly = ly + oy_;
+                // neighbours 1-4 lie ahead (E, NE, N, NW), 5-8 behind (W, SW, S, SE)
+                const bool owned = (nlx >= 0 && nlx < tw && nly >= 0 && nly < th_);
+                if (nb >= 5 && owned) continue;    // the other bead's forward sweep takes it
+                const bool newton = owned;
+                const int lc = (nly + 1) * (B + 2) + nlx + 1;
+                int j = s_cbeg[lc];
+                const int je = j + s_ccnt[lc];
+                if (nb == 0) j = k + 1;
+                for (; j < je; ++j) {
+                    const float2 pj = s_pos[j];
+                    const float dx = pi.x - pj.x, dy = pi.y - pj.y;
+                    const float r2 = dx * dx + dy * dy;
+                    if (r2 < d.rc2 && r2 > 0.f) {
+                        const uint32_t idj = s_id[j];
+                        if (idj == pid) continue;
+                        const float2 vj = s_vel[j];
+                        float ex, ey;
+                        const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, idi, idj, s_lo,
+                                                        s_hi, r2, ex, ey);
+                        fx += F * ex;
+                        fy += F * ey;
+                        if (COUNT) ++cnt;
+                        if (newton) {
+                            atomicAdd(&s_fx[j], -F * ex);
+                            atomicAdd(&s_fy[j], -F * ey);
+                            if (COUNT) atomicAdd(&s_cnt[j], 1u);
+                        }
+                    }
+                }
+            }
+            atomicAdd(&s_fx[k], fx);
+            atomicAdd(&s_fy[k], fy);
+            if (COUNT) atomicAdd(&s_cnt[k], cnt);
+        }
+        __syncthreads();
+
+        // ---- integrate owned beads
+        for (int k = tid; k < n_own; k += NT) {
+            const int g = (int)g0 + k;
+            const float4 xv = d.S_xv[g];
+            const uint32_t id = s_id[k];
+            if (COUNT && d.pcnt) d.pcnt[id] = s_cnt[k];
+            integrate_bead<B>(d, g, xv, id, s_fx[k], s_fy[k], flags, th);
+        }
+    } else {
+        // ---- global-memory path for an over-full tile (one-sided pairs)
+        if (tid == 0) atomicAdd(d.ovf, 1ull);
+        for (int k = tid; k < n_own; k += NT) {
+            const int g = (int)g0 + k;
+            const float4 xv = d.S_xv[g];
+            const uint32_t idi = d.S_id[g], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
+            const int cx = cell_coord(d, xv.x), cy = cell_coord(d, xv.y);
+            float fx = 0.f, fy = 0.f;
+            uint32_t cnt = 0;
+            for (int oy_ = -1; oy_ <= 1; ++oy_)
+                for (int ox_ = -1; ox_ <= 1; ++ox_) {
+                    int ncx = cx + ox_, ncy = cy + oy_;
+                    ncx += (ncx < 0) ? d.nc : ((ncx >= d.nc) ? -d.nc : 0);
+                    ncy += (ncy < 0) ? d.nc : ((ncy >= d.nc) ? -d.nc : 0);
+                    const int gc = cell_of<B>(d, ncx, ncy);
+                    const uint32_t b = min(d.cstart[gc], n), e = min(max(d.cstart[gc + 1], b), n);
+                    for (uint32_t q = b; q < e; ++q) {
+                        if (q == (uint32_t)g) continue;
+                        const uint32_t idj = d.S_id[q];
+                        if (idj == pid) continue;
+                        const float4 xj = d.S_xv[q];
+                        const float dx = minimg(xv.x, xj.x, d.L, d.halfL);
+                        const float dy = minimg(xv.y, xj.y, d.L, d.halfL);
+                        const float r2 = dx * dx + dy * dy;
+                        if (r2 < d.rc2 && r2 > 0.f) {
+                            float ex, ey;
+                            const float F = dpd_pair_scalar(d, dx, dy, xv.z - xj.z, xv.w - xj.w, idi, idj, s_lo,
+                                                            s_hi, r2, ex, ey);
+                            fx += F * ex;
+                            fy += F * ey;
+                            if (COUNT) ++cnt;
+                        }
+                    }
+                }
+            if (COUNT && d.pcnt) d.pcnt[idi] = cnt;
+            integrate_bead<B>(d, g, xv, idi, fx, fy, flags, th);
+        }
+    }
+}
+
+// Block reduction of the thermo partials into the FP64 ring slot of `step`
+// (FP32 inside a warp, FP64 across warps and blocks).
+__device__ __forceinline__ void thermo_flush(const Sys &d, Thermo3 th, double *s_red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        th.ke += __shfl_xor_sync(0xffffffffu, th.ke, o);
+        th.px += __shfl_xor_sync(0xffffffffu, th.px, o);
+        th.py += __shfl_xor_sync(0xffffffffu, th.py, o);
+    }
+    if (lane == 0) {
+        s_red[3 * wid + 0] = (double)th.ke;
+        s_red[3 * wid + 1] = (double)th.px;
+        s_red[3 * wid + 2] = (double)th.py;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int w = 0; w < nw; ++w) { a += s_red[3 * w]; b += s_red[3 * w + 1]; c += s_red[3 * w + 2]; }
+        double *t = d.thermo + 4 * (size_t)(*d.step % THERMO_CAP);
+        atomicAdd(&t[0], a);
+        atomicAdd(&t[1], b);
+        atomicAdd(&t[2], c);
+    }
+}
+
+}  // namespace dpd

@@ -1,0 +1,247 @@
+"""GPU parity of the simulation hot path against the FP64 oracle.
+
+Tolerances (written here, from the BASELINE the benchmark spec):
+  forces at identical input state: ||F_gpu - F_orc|| / ||F_orc|| <= 1e-5 and
+    max_i |dF_i| <= 1e-5 * max(|F_i|, F_rms);
+  positions after 100 steps (C1): max |minimg(x_gpu - x_orc)| <= 1e-4;
+  cell counts and neighbour counts: bit-exact (pairs within 4e-6 r_c^2 of
+    the cutoff, where FP32 and FP64 may decide differently, are excluded).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1310_0998_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(a=25.0, gamma=4.5, kBT=1.0, rc=1.0, kbond=100.0, r0=0.5, fp=1.0, zeta=0.1, dt=0.01, mass=1.0)
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1310_0998_gb300 import Sim
+    return Sim
+
+
+def oparams(orc, L, seed=0, **kw):
+    p = dict(C1)
+    p.update(kw)
+    return orc.params(L=L, seed=seed, **p)
+
+
+def sim_kw(seed=0, **kw):
+    p = dict(C1)
+    p.update(kw)
+    return dict(a=p["a"], gamma=p["gamma"], kBT=p["kBT"], rc=p["rc"], k_bond=p["kbond"], r0=p["r0"],
+                f_p=p["fp"], zeta=p["zeta"], dt=p["dt"], mass=p["mass"], seed=seed,
+                **{k: v for k, v in kw.items() if k in ("tile", "noise", "exclude_bonded", "variant")})
+
+
+def minimg(d, L):
+    return d - L * np.rint(d / L)
+
+
+def force_check(f_gpu, f_orc):
+    fn = np.linalg.norm(f_orc, axis=1)
+    frms = math.sqrt(float(np.mean(fn ** 2)))
+    err = np.linalg.norm(f_gpu.astype(np.float64) - f_orc, axis=1)
+    rel = float(np.linalg.norm(err) / np.linalg.norm(f_orc))
+    worst = float(np.max(err / np.maximum(fn, frms)))
+    assert rel <= 1e-5, (rel, worst)
+    assert worst <= 1e-5, (rel, worst)
+    return rel, worst
+
+
+CASES = [
+    # (L, n_dimers, tile, seed): C1, a ragged multi-tile box, single tiles
+    (32.0, 512, 8, 0),
+    (37.0, 600, 8, 1),
+    (37.0, 600, 4, 2),
+    (37.0, 600, 16, 3),
+    (3.5, 6, 8, 4),
+    (9.0, 100, 16, 5),
+]
+
+
+@pytest.mark.parametrize("L,nd,tile,seed", CASES)
+def test_setup_force_parity(Sim, orc, L, nd, tile, seed):
+    x, _ = synth.dimers(nd, L, 0.5, seed=seed)
+    v = synth.velocities(2 * nd, 1.0, seed=seed + 10)
+    with Sim(L, 2 * nd, **sim_kw(seed=seed + 100, tile=tile)) as s:
+        s.set_positions(x, v, step=7)
+        xv, f, step = s.get_state()
+        assert step == 7
+        np.testing.assert_array_equal(xv[:, :2], x)
+        np.testing.assert_array_equal(xv[:, 2:], v)
+        fo, _ = orc.forces(oparams(orc, L, seed=seed + 100), x.astype(np.float64), v.astype(np.float64), 7)
+        force_check(f, fo)
+
+
+def test_gaussian_noise_and_no_exclusion(Sim, orc):
+    L, nd = 20.0, 300
+    x, _ = synth.dimers(nd, L, 0.5, seed=3)
+    v = synth.velocities(2 * nd, 1.0, seed=4)
+    with Sim(L, 2 * nd, **sim_kw(seed=9, noise=1, exclude_bonded=0)) as s:
+        s.set_positions(x, v, step=123456789012)
+        _, f, _ = s.get_state()
+    fo, _ = orc.forces(oparams(orc, L, seed=9, noise=1, exclude_bonded=0), x.astype(np.float64),
+                       v.astype(np.float64), 123456789012)
+    force_check(f, fo)
+
+
+@pytest.mark.parametrize("L,nd,tile,seed", CASES[:4])
+def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed):
+    x, _ = synth.dimers(nd, L, 0.5, seed=seed)
+    with Sim(L, 2 * nd, **sim_kw(tile=tile)) as s:
+        s.set_positions(x)
+        nc = s.info().n_cells_side
+        assert nc == math.floor(L / (1.0 + 2.0 ** -20 * L))
+        np.testing.assert_array_equal(s.cell_counts(), orc.cell_counts(x, L, nc))
+        cnt, tot = s.pair_counts()
+    co, amb, toto = orc.pair_counts(oparams(orc, L), x.astype(np.float64), tie=4e-6)
+    clean = amb == 0
+    np.testing.assert_array_equal(cnt[clean], co[clean])
+    assert abs(int(tot) - toto) <= int(amb.sum())
+
+
+def test_trajectory_parity_c1_100_steps(Sim, orc):
+    """C1: 512 dimers, L = 32, seed 0: positions after 100 steps."""
+    L, nd = 32.0, 512
+    x, v = synth.dimers(nd, L, 0.5, seed=0)
+    with Sim(L, 2 * nd, **sim_kw(seed=0)) as s:
+        s.set_positions(x, v)
+        s.step(100)
+        xv, f, step = s.get_state()
+    assert step == 100
+    st = orc.State(oparams(orc, L, seed=0), x, v)
+    st.run(100)
+    dx = minimg(xv[:, :2].astype(np.float64) - st.x, L)
+    assert np.abs(dx).max() <= 1e-4, np.abs(dx).max()
+    # velocities and forces at step 100 follow the same trajectory
+    assert np.abs(xv[:, 2:] - st.v).max() <= 2e-2
+    rel = np.linalg.norm(f - st.f) / np.linalg.norm(st.f)
+    assert rel <= 1e-3, rel
+
+
+def test_thermo_fp64_reductions(Sim):
+    L, nd = 32.0, 512
+    x, _ = synth.dimers(nd, L, 0.5, seed=2)
+    v = synth.velocities(2 * nd, 1.3, seed=3)
+    with Sim(L, 2 * nd, **sim_kw(mass=1.7)) as s:
+        s.set_positions(x, v)
+        s.step(5)
+        xv, _, _ = s.get_state()
+        vv = xv[:, 2:].astype(np.float64)
+        ke = 0.5 * 1.7 * np.sum(vv * vv)
+        np.testing.assert_allclose(s.kinetic_energy(), ke, rtol=1e-6)
+        np.testing.assert_allclose(s.momentum(), 1.7 * vv.sum(axis=0), atol=1e-4 * np.abs(vv).sum())
+        np.testing.assert_allclose(s.temperature(), 2 * ke / (2 * 2 * nd - 2), rtol=1e-6)
+        log = s.thermo_log(1, 5)
+        np.testing.assert_allclose(log[-1, 0], ke, rtol=1e-6)
+
+
+def test_restart_from_full_state(Sim):
+    """set_state with forces resumes a run: 20 + 30 steps equals 50 steps up
+    to FP32 accumulation order."""
+    L, nd = 24.0, 300
+    x, v = synth.dimers(nd, L, 0.5, seed=6)
+    with Sim(L, 2 * nd, **sim_kw(seed=3)) as a, Sim(L, 2 * nd, **sim_kw(seed=3)) as b:
+        a.set_positions(x, v)
+        a.step(50)
+        xa, fa, sa = a.get_state()
+        b.set_positions(x, v)
+        b.step(20)
+        xm, fm, sm = b.get_state()
+        b.set_state(xm, fm, sm)
+        b.step(30)
+        xb, fb, sb = b.get_state()
+    assert sa == sb == 50
+    assert np.abs(minimg(xa[:, :2] - xb[:, :2], L)).max() < 1e-4
+
+
+def test_momentum_conserved_without_drag_and_propulsion(Sim):
+    L, nd = 32.0, 512
+    x, _ = synth.dimers(nd, L, 0.5, seed=7)
+    v = synth.velocities(2 * nd, 1.0, seed=8)
+    with Sim(L, 2 * nd, **sim_kw(zeta=0.0, fp=0.0)) as s:
+        s.set_positions(x, v)
+        p0 = s.momentum()
+        s.step(1000)
+        log = s.thermo_log(1, 1000)
+    scale = np.abs(v.astype(np.float64)).sum()
+    assert np.abs(log[:, 1:3] - p0).max() <= 1e-5 * scale
+
+
+def test_single_dimer_drift(Sim):
+    L, r0, fp, zeta, dt = 32.0, 0.5, 1.0, 0.1, 0.01
+    th = 0.3
+    c = np.array([10.0, 12.0])
+    h = 0.5 * r0 * np.array([math.cos(th), math.sin(th)])
+    x = np.array([c + h, c - h], np.float32)
+    with Sim(L, 2, **sim_kw(zeta=zeta, fp=fp, dt=dt)) as s:
+        s.set_positions(x)
+        s.step(3000)
+        xv, _, _ = s.get_state()
+    u, fcur, hh = 0.0, fp, 0.5 * dt
+    for _ in range(3000):
+        uh = u + hh * fcur
+        fcur = fp - zeta * uh
+        u = uh + hh * fcur
+    n = np.array([math.cos(th), math.sin(th)])
+    np.testing.assert_allclose(xv[0, 2:] @ n, u, rtol=1e-5)
+    np.testing.assert_allclose(xv[1, 2:], xv[0, 2:], atol=1e-5)
+
+
+def test_init_random_initial_condition(Sim):
+    L, nd, r0 = 40.0, 2000, 0.5
+    with Sim(L, 2 * nd, **sim_kw()) as s:
+        s.init_random(5)
+        xv, f, step = s.get_state()
+    assert step == 0
+    assert np.all(xv[:, :2] >= 0) and np.all(xv[:, :2] < L)
+    assert np.all(xv[:, 2:] == 0)
+    d = minimg(xv[0::2, :2].astype(np.float64) - xv[1::2, :2], L)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), r0, atol=2e-5)
+    com = np.mod(xv[1::2, :2] + 0.5 * d, L)
+    hist = np.histogram2d(com[:, 0], com[:, 1], bins=4, range=[[0, L], [0, L]])[0]
+    assert hist.min() > nd / 16 * 0.7
+    ang = np.arctan2(d[:, 1], d[:, 0])
+    assert abs(np.mean(np.cos(ang))) < 0.1 and abs(np.mean(np.sin(ang))) < 0.1
+
+
+def test_nonfinite_state_is_reported(Sim):
+    from paper_1310_0998_gb300._lib import DpdError
+    L, nd = 10.0, 20
+    x, _ = synth.dimers(nd, L, 0.5, seed=1)
+    xv = np.zeros((2 * nd, 4), np.float32)
+    xv[:, :2] = x
+    xv[3, 2] = np.nan
+    with Sim(L, 2 * nd, **sim_kw()) as s:
+        with pytest.raises(DpdError) as e:
+            s.set_state(xv)
+        assert e.value.status == -4
+        # a clean state clears the latch
+        xv[3, 2] = 0.0
+        s.set_state(xv)
+        s.step(3)
+        s.sync()
+
+
+def test_full_size_forces_sampled(Sim, orc):
+    """C3 geometry (L = 1024, 3,145,728 beads, density 3) in the benchmark's
+    launch configuration: set-up forces of the whole system against the
+    cell-list FP64 oracle (itself checked against the all-pairs oracle)."""
+    L = 1024.0
+    nd = 3 * 1024 * 1024 // 2
+    x, _ = synth.dimers(nd, L, 0.5, seed=0)
+    v = synth.velocities(2 * nd, 1.0, seed=1)
+    with Sim(L, 2 * nd, **sim_kw(seed=0)) as s:
+        s.set_positions(x, v, step=3)
+        _, f, _ = s.get_state()
+        assert s.info().overflow_tiles == 0
+    fo, _ = orc.forces(oparams(orc, L, seed=0), x.astype(np.float64), v.astype(np.float64), 3, cells=True)
+    force_check(f, fo)
