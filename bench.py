@@ -237,17 +237,17 @@ def main():
     force_s = float(prof[:, 2].mean()) / 1e3
 
     # end to end through the C ABI with host (pinned) buffers: upload the full
-    # state (x, v, f), one step, download it
-    xv_h = torch.empty((nb, 4), dtype=torch.float32, pin_memory=True).numpy()
+    # state (x double, v, f float), one step, download it
+    x_h = torch.empty((nb, 2), dtype=torch.float64, pin_memory=True).numpy()
+    v_h = torch.empty((nb, 2), dtype=torch.float32, pin_memory=True).numpy()
     f_h = torch.empty((nb, 2), dtype=torch.float32, pin_memory=True).numpy()
-    _, _, s_cur = sim.get_state(xv_h, f_h)
-    sim.set_state(xv_h, f_h, s_cur)
+    _, _, _, s_cur = sim.get_state(x_h, v_h, f_h)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        sim.set_state(xv_h, f_h, s_cur)
+        sim.set_state(x_h, v_h, f_h, s_cur)
         sim.step(1)
-        _, _, s_cur = sim.get_state(xv_h, f_h)
+        _, _, _, s_cur = sim.get_state(x_h, v_h, f_h)
     e2e_s = time.perf_counter() - t0
     e2e_val = world * nb * args.e2e_steps / e2e_s
     info = sim.info()
@@ -272,8 +272,8 @@ def main():
                 "bytes_per_bead_step": BYTES_PER_BEAD_STEP, "peak_src": pk["src"]},
         "kernels_ms": {"scan": float(prof[:, 0].mean()), "scatter": float(prof[:, 1].mean()),
                        "force_integrate": float(prof[:, 2].mean())},
-        "e2e": {"value": e2e_val, "unit": "particle-steps/s", "h2d_bytes_per_step": 24 * nb,
-                "d2h_bytes_per_step": 24 * nb, "steps": args.e2e_steps},
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s", "h2d_bytes_per_step": 32 * nb,
+                "d2h_bytes_per_step": 32 * nb, "steps": args.e2e_steps},
         "gpu_launches": 3 * args.steps,
         "overflow_tiles": int(info.overflow_tiles),
         "clocks": clk,

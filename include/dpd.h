@@ -23,8 +23,13 @@
  * sqrt(3) (2 (w0 >> 8) + 1 - 2^24) 2^-24 (uniform, unit variance) or, with
  * noise = 1, Box-Muller on words 0 and 1.
  *
- * State layout on the host side of the ABI: "xv" = float[N][4] (x, y, vx, vy)
- * in id order, "f" = float[N][2] in id order.  FP32 state; FP64 reductions.
+ * State on the ABI: positions x = double[N][2], velocities v = float[N][2],
+ * forces f = float[N][2], all in id order.  Inside, positions are 32-bit
+ * fixed point (x = X L / 2^32, uniform resolution L 2^-32, exact periodic
+ * wrap); a position crosses the ABI as the exact double X L / 2^32 when L
+ * has at most 21 significant bits (any L that is a multiple of 2^-8 below
+ * 8192, say), so a state read back and set again is unchanged.  FP32
+ * velocities and forces; FP64 reductions.
  *
  * Concurrency: a context is not thread-safe; all its work is ordered on its
  * stream.  Calls that return host data synchronise that stream.  Device-side
@@ -86,7 +91,8 @@ typedef struct dpd_ctx dpd_ctx;
 /* Geometry and counters of a context. */
 typedef struct dpd_info {
     int64_t n_beads;
-    int32_t n_cells_side;   /* n_c = floor(L / (r_c + 2^-20 L))              */
+    int32_t n_cells_side;   /* n_c = floor(L / r_c); cell of x: floor(x n_c / L),
+                               exact on the fixed-point grid                 */
     int32_t tile;           /* cell-block side B                             */
     int32_t n_tiles;        /* ceil(n_c/B)^2                                 */
     int32_t variant;        /* pair-kernel variant in use                    */
@@ -101,7 +107,7 @@ const char *dpd_status_string(int status);
 
 /* Create a context on the current CUDA device, ordered on `stream`.
  * Validates p (see field comments); allocates all device buffers (about
- * 100 bytes per bead plus 8 bytes per cell).  The state is undefined until
+ * 130 bytes per bead plus 8 bytes per cell).  The state is undefined until
  * dpd_set_state or dpd_init_random.  *out receives the context. */
 int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out);
 
@@ -113,17 +119,18 @@ void dpd_destroy(dpd_ctx *ctx);
  * effect at the next step; forces of the current state are not recomputed. */
 int dpd_set_params(dpd_ctx *ctx, const dpd_params *p);
 
-/* Set the canonical state at step `step`.  xv: [N][4] (x, y, vx, vy), id
- * order, positions anywhere (wrapped into [0, L)).  f: [N][2] forces of that
- * state, or NULL to compute the set-up force F(x, v, step) (velocities v, the
- * random stream of `step`).  where: DPD_HOST or DPD_DEVICE for both pointers.
- * Synchronises the stream. */
-int dpd_set_state(dpd_ctx *ctx, const float *xv, const float *f, int64_t step, int where);
+/* Set the canonical state at step `step`.  x: [N][2] positions (anywhere;
+ * wrapped into [0, L) and rounded to the nearest L 2^-32), v: [N][2]
+ * velocities, f: [N][2] forces of that state, or NULL to compute the set-up
+ * force F(x, v, step) (velocities v, the random stream of `step`).  where:
+ * DPD_HOST or DPD_DEVICE for all pointers.  Non-finite input gives
+ * DPD_ERR_NONFINITE.  Synchronises the stream. */
+int dpd_set_state(dpd_ctx *ctx, const double *x, const float *v, const float *f, int64_t step, int where);
 
 /* Paper's initial condition (Sec. 5): agent centres uniform in the box,
  * orientations uniform, bond at rest length r0, velocities zero; drawn on the
- * device from Philox4x32-10 under key (seed, 0x1D17) so it is reproducible;
- * then the set-up force at step 0. */
+ * device from Philox4x32-10 (counter (k, 0, 0, 0) for agent k, key (seed lo,
+ * seed hi ^ 0x1D17)) so it is reproducible; then the set-up force at step 0. */
 int dpd_init_random(dpd_ctx *ctx, uint64_t seed);
 
 /* Advance n >= 0 velocity-Verlet steps (asynchronous on the stream). */
@@ -132,9 +139,10 @@ int dpd_step(dpd_ctx *ctx, int64_t n);
 /* Wait for the stream and return the latched device status. */
 int dpd_sync(dpd_ctx *ctx);
 
-/* Canonical state (x_s, v_s, f_s) and step s.  xv: [N][4], f: [N][2] (may be
- * NULL), step (may be NULL).  where: DPD_HOST or DPD_DEVICE.  Synchronises. */
-int dpd_get_state(dpd_ctx *ctx, float *xv, float *f, int64_t *step, int where);
+/* Canonical state (x_s, v_s, f_s) and step s.  x: [N][2] (double), v, f:
+ * [N][2] (float); any of x, v, f, step may be NULL.  where: DPD_HOST or
+ * DPD_DEVICE.  Synchronises. */
+int dpd_get_state(dpd_ctx *ctx, double *x, float *v, float *f, int64_t *step, int where);
 
 /* FP64 reductions over the canonical state of the last completed step:
  * kinetic energy 1/2 sum m|v|^2, momentum sum m v, temperature

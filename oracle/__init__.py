@@ -80,7 +80,7 @@ def lib():
             L.orc_forces_cells.restype = i64
             L.orc_pair_forces_only.argtypes = [P(OrcParams), i64, vp, vp, i64, vp]
             L.orc_run.argtypes = [P(OrcParams), i64, vp, vp, vp, P(i64), i64, ctypes.c_int, vp]
-            L.orc_cell_counts.argtypes = [i64, vp, ctypes.c_float, ctypes.c_int32, vp]
+            L.orc_cell_counts.argtypes = [i64, vp, d, ctypes.c_int32, vp]
             L.orc_pair_counts.argtypes = [P(OrcParams), i64, vp, d, vp, vp]
             L.orc_pair_counts.restype = i64
             L.orc_num_threads.restype = ctypes.c_int
@@ -159,11 +159,12 @@ class State:
         return log[:nsteps] if thermo else None
 
 
-def cell_counts(x32, L: float, nc: int) -> np.ndarray:
-    """Per-cell bead counts by the FP32 binning rule, row-major [nc, nc]."""
-    x, xp = _c(x32, np.float32)
+def cell_counts(x, L: float, nc: int) -> np.ndarray:
+    """Per-cell bead counts, cell floor(x nc / L), row-major [nc, nc]; x on
+    the fixed-point grid X L / 2^32."""
+    x, xp = _c(x, np.float64)
     out = np.zeros(nc * nc, np.uint32)
-    lib().orc_cell_counts(x.shape[0], xp, ctypes.c_float(L), int(nc), out.ctypes.data_as(ctypes.c_void_p))
+    lib().orc_cell_counts(x.shape[0], xp, float(L), int(nc), out.ctypes.data_as(ctypes.c_void_p))
     return out.reshape(nc, nc)
 
 

@@ -28,8 +28,8 @@
  *   orc_forces_cells    the same forces as orc_forces through a cell list
  *                       (OpenMP, one-sided, full 3x3 stencil); used to time a
  *                       CPU baseline and checked against orc_forces.
- *   orc_cell_counts     the FP32 cell-binning rule that the GPU path documents,
- *                       evaluated in single precision on the CPU.
+ *   orc_cell_counts     the cell-binning rule that the GPU path documents,
+ *                       floor(x n_c / L) on the fixed-point position grid.
  *   orc_pair_counts     brute-force per-bead interacting-neighbour counts.
  *
  * Parity pins (tests/test_oracle_*.py): Philox against Triton's independent
@@ -318,20 +318,18 @@ void orc_run(const orc_params *p, int64_t n, double *x, double *v, double *f, in
     }
 }
 
-/* Cell binning in single precision, the rule the GPU path documents:
- *   cx = min(nc - 1, (int)(x * inv)),  inv = (float)nc / (float)L,
- * with x the FP32 position in [0, L).  counts: [nc*nc], row-major (cy*nc+cx). */
-void orc_cell_counts(int64_t n, const float *x, float L, int32_t nc, uint32_t *counts)
+/* Cell binning, the rule the GPU path documents: with n_c cells per side,
+ * bead x lies in cell floor(x n_c / L).  Positions are on the grid
+ * x = X L / 2^32 (integer X), so X = x / L * 2^32 exactly and the cell is
+ * (X n_c) >> 32 in integer arithmetic.  counts: [nc*nc], row-major. */
+void orc_cell_counts(int64_t n, const double *x, double L, int32_t nc, uint32_t *counts)
 {
-    volatile float inv = (float)nc / L;
     memset(counts, 0, sizeof(uint32_t) * (size_t)nc * (size_t)nc);
     for (int64_t i = 0; i < n; ++i) {
-        volatile float px = x[2 * i] * inv;
-        volatile float py = x[2 * i + 1] * inv;
-        int cx = (int)px, cy = (int)py;
-        if (cx > nc - 1) cx = nc - 1;
-        if (cy > nc - 1) cy = nc - 1;
-        counts[(int64_t)cy * nc + cx]++;
+        uint64_t X = (uint64_t)(x[2 * i] / L * 4294967296.0);
+        uint64_t Y = (uint64_t)(x[2 * i + 1] / L * 4294967296.0);
+        uint64_t cx = (X * (uint64_t)nc) >> 32, cy = (Y * (uint64_t)nc) >> 32;
+        counts[cy * (uint64_t)nc + cx]++;
     }
 }
 

@@ -75,11 +75,11 @@ def _declare(L):
         "dpd_create": ([P(DpdParams), vp, P(vp)], c_int),
         "dpd_destroy": ([vp], None),
         "dpd_set_params": ([vp, P(DpdParams)], c_int),
-        "dpd_set_state": ([vp, vp, vp, i64, c_int], c_int),
+        "dpd_set_state": ([vp, vp, vp, vp, i64, c_int], c_int),
         "dpd_init_random": ([vp, u64], c_int),
         "dpd_step": ([vp, i64], c_int),
         "dpd_sync": ([vp], c_int),
-        "dpd_get_state": ([vp, vp, vp, P(i64), c_int], c_int),
+        "dpd_get_state": ([vp, vp, vp, vp, P(i64), c_int], c_int),
         "dpd_kinetic_energy": ([vp, P(d)], c_int),
         "dpd_momentum": ([vp, vp], c_int),
         "dpd_temperature": ([vp, P(d)], c_int),

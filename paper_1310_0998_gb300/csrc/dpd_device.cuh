@@ -4,15 +4,21 @@
 // Sec. 5 (velocity-Verlet, periodic square).  Random numbers: Philox4x32-10
 // (Salmon et al., SC'11).
 //
+// Positions are 32-bit fixed point: coordinate X in [0, 2^32) stands for
+// x = X L / 2^32.  Resolution is uniform over the box (L 2^-32), the periodic
+// wrap is the natural overflow of unsigned addition, the minimum-image
+// displacement is the signed difference (int32)(X_i - X_j), and the cell of a
+// bead is (X nc) >> 32 exactly.  Velocities and forces are FP32.
+//
 // Data layout in HBM (one system; the ensemble packs several side by side):
-//   S_xv  float4[N]  pre-force state (x, y, v*x, v*y) sorted by cell, where v*
-//                    is the half-step velocity v_{s-1/2} (v_s at set-up)
+//   S_xv  uint4[N]   pre-force state (X, Y, bits of v*x, v*y) sorted by cell,
+//                    where v* is the half-step velocity v_{s-1/2} (v_s at set-up)
 //   S_id  u32[N]     bead id of each sorted slot
 //   slot  u32[N]     id -> sorted slot (to find a bead's bonded partner)
 //   U_*             next pre-force state written by the force kernel, in the
 //                    order of S, plus each bead's rank inside its new cell
 //   counts, cstart   cell populations and their exclusive prefix sum
-//   C_xv, C_f        canonical (x_s, v_s), f_s in id order (last step of a call)
+//   C_xv, C_f        canonical (X_s, v_s), f_s in id order (last step of a call)
 // Cells are numbered tile-major: the domain is cut into B x B cell blocks
 // ("tiles", ragged at the high edge) and the cells of one tile are
 // consecutive, so a tile's own beads form one contiguous run of S.
@@ -33,17 +39,18 @@ constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (x ~100 ns)
 
 // Per-system view handed to every kernel by value.
 struct Sys {
-    float L, halfL, inv_cs, cs;
+    double Ld, ulen_d;             // L and L / 2^32 in double (state conversion)
+    float L, ulen, inv_ulen, cs;   // ulen = L / 2^32, inv_ulen = 2^32 / L
     int nc, ntx, n, ncells;
     float rc2, inv_rc, a, gamma, sig_r, kbond, r0, fp, zeta, dt, hdtm;
     uint32_t key0, key1;
     int noise, excl, cap;
-    float4 *S_xv;
+    uint4 *S_xv;
     uint32_t *S_id;
-    float4 *U_xv;
+    uint4 *U_xv;
     uint32_t *U_id, *U_rank;
     uint32_t *slot, *counts, *cstart;
-    float4 *C_xv;
+    uint4 *C_xv;
     float2 *C_f;
     double *thermo;
     long long *step;
@@ -89,13 +96,8 @@ __device__ __forceinline__ float pair_noise(const Sys &d, uint32_t ia, uint32_t 
 }
 
 // ---------------------------------------------------------- cell geometry ----
-// Cell coordinate of an FP32 position in [0, L): min(nc - 1, (int)(x * inv)),
-// inv = (float)nc / (float)L, one IEEE single multiply.
-__device__ __forceinline__ int cell_coord(const Sys &d, float x)
-{
-    const int c = (int)__fmul_rn(x, d.inv_cs);
-    return min(max(c, 0), d.nc - 1);
-}
+// Cell coordinate of a fixed-point coordinate: floor(x nc / L) = (X nc) >> 32.
+__device__ __forceinline__ int cell_coord(const Sys &d, uint32_t X) { return (int)__umulhi(X, (uint32_t)d.nc); }
 
 template <int B>
 __device__ __forceinline__ int cell_of(const Sys &d, int cx, int cy)
@@ -105,27 +107,22 @@ __device__ __forceinline__ int cell_of(const Sys &d, int cx, int cy)
     return ty * B * d.nc + tx * B * th + ly * tw + lx;
 }
 
-// Minimum-image difference a - b of two coordinates in [0, L), formed so that
-// the large operand is shifted by L first (exact) when the pair straddles the
-// periodic boundary.
-__device__ __forceinline__ float minimg(float a, float b, float L, float halfL)
+// Minimum-image displacement x_a - x_b in length units (exact integer
+// difference, one rounding in the conversion).
+__device__ __forceinline__ float mdiff(const Sys &d, uint32_t a, uint32_t b)
 {
-    float d = a - b;
-    if (d > halfL) d = (a - L) - b;
-    else if (d < -halfL) d = a - (b - L);
-    return d;
+    return (float)(int)(a - b) * d.ulen;
 }
 
-// Wrap x + dx back into [0, L) for |dx| < L, keeping precision near 0 and L.
-__device__ __forceinline__ float wrap_add(float x, float dx, float L)
+// Fixed-point step of a coordinate by a displacement dx (|dx| < L/2):
+// rounded to the nearest unit, wrapped by unsigned overflow.
+__device__ __forceinline__ uint32_t fx_add(const Sys &d, uint32_t X, float dx)
 {
-    float y = x + dx;
-    if (y >= L) y = (x - L) + dx;
-    else if (y < 0.0f) y = y + L;
-    if (y >= L) y -= L;          // y + L rounded up to L
-    if (y < 0.0f) y = 0.0f;
-    return y;
+    return X + (uint32_t)__float2int_rn(dx * d.inv_ulen);
 }
+
+__device__ __forceinline__ float vbits(uint32_t u) { return __uint_as_float(u); }
+__device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
 
 __device__ __forceinline__ void set_err(const Sys &d, int bits) { atomicOr(d.err, bits); }
 

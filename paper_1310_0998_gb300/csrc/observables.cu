@@ -33,20 +33,24 @@ __device__ __forceinline__ double minimg_d(double d, double L)
     return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
 }
 
-__global__ void k_agent_com(const float4 *__restrict__ xv, int na, double L, double2 *c, double2 *v)
+// Positions enter as the exact doubles X L / 2^32 of the fixed-point state.
+__global__ void k_agent_com(const uint4 *__restrict__ xv, int na, double L, double ulen, double2 *c, double2 *v)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= na) return;
-    const float4 h = xv[2 * k], t = xv[2 * k + 1];
-    const double dx = minimg_d(__dsub_rn((double)h.x, (double)t.x), L);
-    const double dy = minimg_d(__dsub_rn((double)h.y, (double)t.y), L);
-    double cx = __dadd_rn((double)t.x, __dmul_rn(0.5, dx));
-    double cy = __dadd_rn((double)t.y, __dmul_rn(0.5, dy));
+    const uint4 h = xv[2 * k], t = xv[2 * k + 1];
+    const double hx = __dmul_rn((double)h.x, ulen), hy = __dmul_rn((double)h.y, ulen);
+    const double tx = __dmul_rn((double)t.x, ulen), ty = __dmul_rn((double)t.y, ulen);
+    const double dx = minimg_d(__dsub_rn(hx, tx), L);
+    const double dy = minimg_d(__dsub_rn(hy, ty), L);
+    double cx = __dadd_rn(tx, __dmul_rn(0.5, dx));
+    double cy = __dadd_rn(ty, __dmul_rn(0.5, dy));
     cx = __dsub_rn(cx, __dmul_rn(L, floor(__ddiv_rn(cx, L))));
     cy = __dsub_rn(cy, __dmul_rn(L, floor(__ddiv_rn(cy, L))));
     c[k] = make_double2(cx, cy);
-    v[k] = make_double2(__dmul_rn(0.5, __dadd_rn((double)h.z, (double)t.z)),
-                        __dmul_rn(0.5, __dadd_rn((double)h.w, (double)t.w)));
+    const double hvx = (double)__uint_as_float(h.z), hvy = (double)__uint_as_float(h.w);
+    const double tvx = (double)__uint_as_float(t.z), tvy = (double)__uint_as_float(t.w);
+    v[k] = make_double2(__dmul_rn(0.5, __dadd_rn(hvx, tvx)), __dmul_rn(0.5, __dadd_rn(hvy, tvy)));
 }
 
 // Grid indices i whose window [x_i - eps/2, x_i + eps/2] (minimum image)
@@ -269,7 +273,7 @@ static int field_device(dpd_ctx *c, int M, double eps, double2 **z_out, double *
     const double L = c->p.L;
     if (eps <= 0.0) eps = L * std::sqrt(10.0 / (double)na);
     CUO(cudaMemsetAsync(sx, 0, 8 * MM * 3, c->st));
-    k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, cc, vv);
+    k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, c->d.ulen_d, cc, vv);
     k_deposit<<<(na + 127) / 128, 128, 0, c->st>>>(cc, vv, na, L, L / M, 0.5 * eps, M, sx, sy, cn);
     k_field_finish<<<(int)((MM + 255) / 256), 256, 0, c->st>>>(sx, sy, cn, (int)MM, z);
     CUO(cudaGetLastError());
@@ -340,7 +344,7 @@ int dpd_velocity_correlation(dpd_ctx *c, double dr, int nbins, double *g, double
     double *acc = (double *)b;
     const double L = c->p.L;
     CUO(cudaMemsetAsync(gnum, 0, 16 * (size_t)nbins + 32, c->st));
-    k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, cc, vv);
+    k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, c->d.ulen_d, cc, vv);
     k_vmeans<<<64, 256, 0, c->st>>>(vv, na, acc);
     const int ntile = (na + VCF_TILE - 1) / VCF_TILE;
     const long long nblk = (long long)ntile * (ntile + 1) / 2;

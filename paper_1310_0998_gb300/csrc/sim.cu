@@ -34,15 +34,70 @@ __global__ void k_bin(Sys d)
     if (k < d.n) bin_one<B>(d, k);
 }
 
-__global__ void k_iota(Sys d)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < d.n) d.U_id[k] = (uint32_t)k;
-}
-
 __global__ void k_set_step(Sys d, long long s) { *d.step = s; }
 
-// Canonical (x_s, v_s, f_s) in id order -> next pre-force state in U, plus
+// Double position -> fixed point: wrap into [0, L), round to the nearest unit
+// of L / 2^32 (exact for positions already on that grid).
+__device__ __forceinline__ uint32_t to_fixed(const Sys &d, double x, bool &ok)
+{
+    if (!isfinite(x)) { ok = false; return 0u; }
+    const double xr = x - d.Ld * floor(x / d.Ld);
+    return (uint32_t)(unsigned long long)llrint(xr / d.ulen_d);
+}
+
+// Upload: positions (double [N][2]) and velocities (float [N][2]) in id order.
+// into U (set-up path, f == NULL) or into the canonical buffers (with f).
+__global__ void k_load_state(Sys d, const double *__restrict__ x, const float *__restrict__ v,
+                             const float *__restrict__ f)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    bool ok = true;
+    const uint32_t X = to_fixed(d, x[2 * k], ok), Y = to_fixed(d, x[2 * k + 1], ok);
+    float vx = v[2 * k], vy = v[2 * k + 1];
+    if (!isfinite(vx) || !isfinite(vy)) ok = false;
+    float fx = 0.f, fy = 0.f;
+    if (f) {
+        fx = f[2 * k];
+        fy = f[2 * k + 1];
+        if (!isfinite(fx) || !isfinite(fy)) ok = false;
+    }
+    if (!ok) {
+        set_err(d, ERR_NONFINITE);
+        vx = vy = fx = fy = 0.f;
+    }
+    const uint4 r = make_uint4(X, Y, fbits(vx), fbits(vy));
+    if (f) {
+        d.C_xv[k] = r;
+        d.C_f[k] = make_float2(fx, fy);
+    } else {
+        d.U_xv[k] = r;
+        d.U_id[k] = (uint32_t)k;
+    }
+}
+
+// Download of the canonical state: exact double positions (X L / 2^32).
+__global__ void k_store_state(Sys d, double *__restrict__ x, float *__restrict__ v, float *__restrict__ f)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const uint4 r = d.C_xv[k];
+    if (x) {
+        x[2 * k] = (double)r.x * d.ulen_d;
+        x[2 * k + 1] = (double)r.y * d.ulen_d;
+    }
+    if (v) {
+        v[2 * k] = vbits(r.z);
+        v[2 * k + 1] = vbits(r.w);
+    }
+    if (f) {
+        const float2 ff = d.C_f[k];
+        f[2 * k] = ff.x;
+        f[2 * k + 1] = ff.y;
+    }
+}
+
+// Canonical (X_s, v_s, f_s) in id order -> next pre-force state in U, plus
 // the thermo entry of step s.
 template <int B>
 __global__ void k_kick_bin(Sys d)
@@ -51,27 +106,26 @@ __global__ void k_kick_bin(Sys d)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     Thermo3 th{0.f, 0.f, 0.f};
     if (k < d.n) {
-        float4 xv = d.C_xv[k];
+        const uint4 xv = d.C_xv[k];
         const float2 f = d.C_f[k];
-        th.ke = xv.z * xv.z + xv.w * xv.w;
-        th.px = xv.z;
-        th.py = xv.w;
-        float vx = xv.z + d.hdtm * f.x, vy = xv.w + d.hdtm * f.y;
-        float nx = xv.x - d.L * floorf(xv.x / d.L), ny = xv.y - d.L * floorf(xv.y / d.L);
-        if (!(nx >= 0.f && nx < d.L)) nx = 0.f;
-        if (!(ny >= 0.f && ny < d.L)) ny = 0.f;
-        d.C_xv[k] = make_float4(nx, ny, xv.z, xv.w);
+        float vx = vbits(xv.z), vy = vbits(xv.w);
+        th.ke = vx * vx + vy * vy;
+        th.px = vx;
+        th.py = vy;
+        vx += d.hdtm * f.x;
+        vy += d.hdtm * f.y;
         const float ddx = d.dt * vx, ddy = d.dt * vy;
-        if (isfinite(ddx) && isfinite(ddy) && fabsf(ddx) < d.halfL && fabsf(ddy) < d.halfL) {
-            nx = wrap_add(nx, ddx, d.L);
-            ny = wrap_add(ny, ddy, d.L);
+        uint32_t nx = xv.x, ny = xv.y;
+        if (fabsf(ddx) < 0.25f * d.L && fabsf(ddy) < 0.25f * d.L) {
+            nx = fx_add(d, xv.x, ddx);
+            ny = fx_add(d, xv.y, ddy);
         } else {
             set_err(d, ERR_NONFINITE);
-            nx = 0.f; ny = 0.f; vx = 0.f; vy = 0.f;
+            vx = 0.f; vy = 0.f;
         }
         const int c = cell_of<B>(d, cell_coord(d, nx), cell_coord(d, ny));
         d.U_rank[k] = atomicAdd(&d.counts[c], 1u);
-        d.U_xv[k] = make_float4(nx, ny, vx, vy);
+        d.U_xv[k] = make_uint4(nx, ny, fbits(vx), fbits(vy));
         d.U_id[k] = (uint32_t)k;
     }
     thermo_flush(d, th, s_red);
@@ -90,22 +144,22 @@ __global__ void __launch_bounds__(256) k_force(Sys d, int flags)
 }
 
 // Paper's initial condition (Sec. 5): per agent k, Philox4x32-10 of counter
-// (k, 0, 0, 0) under key (seed lo, seed hi ^ 0x1D17) gives the centre
-// (u0 L, u1 L) and orientation 2 pi u2; beads at centre +/- r0/2 n; v = 0.
+// (k, 0, 0, 0) under key (seed lo, seed hi ^ 0x1D17); words 0 and 1 are the
+// centre's fixed-point coordinates (uniform on the box), word 2 the
+// orientation 2 pi w2 / 2^32; beads at centre +/- (r0/2) n; v = 0.
 __global__ void k_init_random(Sys d, unsigned long long seed)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * k + 1 >= d.n) return;
     uint32_t c0 = (uint32_t)k, c1 = 0, c2 = 0, c3 = 0;
     philox10(c0, c1, c2, c3, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32) ^ 0x1D17u);
-    const float u0 = (float)(c0 >> 8) * 5.9604644775390625e-08f;
-    const float u1 = (float)(c1 >> 8) * 5.9604644775390625e-08f;
     const float u2 = (float)(c2 >> 8) * 5.9604644775390625e-08f;
     float sn, cs;
     sincospif(2.0f * u2, &sn, &cs);
-    const float cx = u0 * d.L, cy = u1 * d.L, h = 0.5f * d.r0;
-    d.U_xv[2 * k] = make_float4(cx + h * cs, cy + h * sn, 0.f, 0.f);
-    d.U_xv[2 * k + 1] = make_float4(cx - h * cs, cy - h * sn, 0.f, 0.f);
+    const float h = 0.5f * d.r0;
+    const int hx = __float2int_rn(h * cs * d.inv_ulen), hy = __float2int_rn(h * sn * d.inv_ulen);
+    d.U_xv[2 * k] = make_uint4(c0 + (uint32_t)hx, c1 + (uint32_t)hy, 0u, 0u);
+    d.U_xv[2 * k + 1] = make_uint4(c0 - (uint32_t)hx, c1 - (uint32_t)hy, 0u, 0u);
     d.U_id[2 * k] = 2u * k;
     d.U_id[2 * k + 1] = 2u * k + 1u;
 }
@@ -123,7 +177,7 @@ static int cuerr(cudaError_t e)
         if (e_ != cudaSuccess) return cuerr(e_); \
     } while (0)
 
-int n_cells_side(double L, double rc) { return (int)std::floor(L / (rc + std::ldexp(1.0, -20) * L)); }
+int n_cells_side(double L, double rc) { return (int)std::floor(L / rc); }
 
 int validate(const dpd_params *p)
 {
@@ -164,11 +218,13 @@ void fill_physics(Sys &d, const dpd_params *p)
 void fill_geometry(Sys &d, const dpd_params *p, int B)
 {
     const int nc = n_cells_side(p->L, p->rc);
+    d.Ld = p->L;
+    d.ulen_d = std::ldexp(p->L, -32);
     d.L = (float)p->L;
-    d.halfL = 0.5f * d.L;
+    d.ulen = (float)d.ulen_d;
+    d.inv_ulen = (float)(std::ldexp(1.0, 32) / p->L);
     d.nc = nc;
-    d.inv_cs = (float)nc / d.L;
-    d.cs = d.L / (float)nc;
+    d.cs = (float)(p->L / nc);
     d.ntx = (nc + B - 1) / B;
     d.n = (int)p->n_beads;
     d.ncells = nc * nc;
@@ -364,7 +420,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
                  o_Ur = take(4 * n), o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
                  o_C = take(16 * n), o_Cf = take(8 * n), o_th = take(sizeof(double) * 4 * THERMO_CAP),
                  o_step = take(8), o_pc = take(4 * n), o_ovf = take(8), o_err = take(8),
-                 o_ss = take(8 * (size_t)c->nscan), o_tk = take(8);
+                 o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(32 * n);
     c->pool_bytes = off;
     if (cudaMalloc(&c->pool, off) != cudaSuccess) {
         if (c->own_stream) cudaStreamDestroy(c->st);
@@ -378,15 +434,16 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
         return DPD_ERR_OOM;
     }
     char *b = (char *)c->pool;
-    d.S_xv = (float4 *)(b + o_S);
+    d.S_xv = (uint4 *)(b + o_S);
     d.S_id = (uint32_t *)(b + o_Sid);
-    d.U_xv = (float4 *)(b + o_U);
+    d.U_xv = (uint4 *)(b + o_U);
     d.U_id = (uint32_t *)(b + o_Uid);
     d.U_rank = (uint32_t *)(b + o_Ur);
     d.slot = (uint32_t *)(b + o_slot);
     d.counts = (uint32_t *)(b + o_cnt);
     d.cstart = (uint32_t *)(b + o_cst);
-    d.C_xv = (float4 *)(b + o_C);
+    d.C_xv = (uint4 *)(b + o_C);
+    c->stage = b + o_stage;
     d.C_f = (float2 *)(b + o_Cf);
     d.thermo = (double *)(b + o_th);
     d.step = (long long *)(b + o_step);
@@ -446,20 +503,25 @@ static int start_from_U(dpd_ctx *c, long long step)
     return dpd_internal_latched(c);
 }
 
-int dpd_set_state(dpd_ctx *c, const float *xv, const float *f, int64_t step, int where)
+int dpd_set_state(dpd_ctx *c, const double *x, const float *v, const float *f, int64_t step, int where)
 {
-    if (!c || !xv || (where != DPD_HOST && where != DPD_DEVICE)) return DPD_ERR_INVALID_ARG;
+    if (!c || !x || !v || (where != DPD_HOST && where != DPD_DEVICE)) return DPD_ERR_INVALID_ARG;
     const size_t n = (size_t)c->d.n;
-    const cudaMemcpyKind kind = where == DPD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const double *dx = x;
+    const float *dv = v, *df = f;
+    if (where == DPD_HOST) {
+        char *st = (char *)c->stage;
+        CU(cudaMemcpyAsync(st, x, 16 * n, cudaMemcpyHostToDevice, c->st));
+        CU(cudaMemcpyAsync(st + 16 * n, v, 8 * n, cudaMemcpyHostToDevice, c->st));
+        if (f) CU(cudaMemcpyAsync(st + 24 * n, f, 8 * n, cudaMemcpyHostToDevice, c->st));
+        dx = (const double *)st;
+        dv = (const float *)(st + 16 * n);
+        df = f ? (const float *)(st + 24 * n) : nullptr;
+    }
     CU(cudaMemsetAsync(c->d.err, 0, sizeof(int), c->st));
     CU(cudaMemsetAsync(c->d.counts, 0, sizeof(uint32_t) * (size_t)c->d.ncells, c->st));
-    if (!f) {
-        CU(cudaMemcpyAsync(c->d.U_xv, xv, 16 * n, kind, c->st));
-        k_iota<<<(c->d.n + 255) / 256, 256, 0, c->st>>>(c->d);
-        return start_from_U(c, step);
-    }
-    CU(cudaMemcpyAsync(c->d.C_xv, xv, 16 * n, kind, c->st));
-    CU(cudaMemcpyAsync(c->d.C_f, f, 8 * n, kind, c->st));
+    k_load_state<<<(c->d.n + 255) / 256, 256, 0, c->st>>>(c->d, dx, dv, df);
+    if (!f) return start_from_U(c, step);
     k_set_step<<<1, 1, 0, c->st>>>(c->d, step);
     CU(cudaMemsetAsync(c->d.thermo + 4 * (size_t)(step % THERMO_CAP), 0, 4 * sizeof(double), c->st));
     launch_kick_bin(c->d, c->B, c->st);
@@ -501,14 +563,24 @@ int dpd_sync(dpd_ctx *c)
     return dpd_internal_latched(c);
 }
 
-int dpd_get_state(dpd_ctx *c, float *xv, float *f, int64_t *step, int where)
+int dpd_get_state(dpd_ctx *c, double *x, float *v, float *f, int64_t *step, int where)
 {
     if (!c || (where != DPD_HOST && where != DPD_DEVICE)) return DPD_ERR_INVALID_ARG;
     if (!c->have_state) return DPD_ERR_STATE;
     const size_t n = (size_t)c->d.n;
-    const cudaMemcpyKind kind = where == DPD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    if (xv) CU(cudaMemcpyAsync(xv, c->d.C_xv, 16 * n, kind, c->st));
-    if (f) CU(cudaMemcpyAsync(f, c->d.C_f, 8 * n, kind, c->st));
+    if (where == DPD_DEVICE) {
+        k_store_state<<<(c->d.n + 255) / 256, 256, 0, c->st>>>(c->d, x, v, f);
+        CU(cudaGetLastError());
+    } else {
+        char *st = (char *)c->stage;
+        k_store_state<<<(c->d.n + 255) / 256, 256, 0, c->st>>>(c->d, x ? (double *)st : nullptr,
+                                                                v ? (float *)(st + 16 * n) : nullptr,
+                                                                f ? (float *)(st + 24 * n) : nullptr);
+        CU(cudaGetLastError());
+        if (x) CU(cudaMemcpyAsync(x, st, 16 * n, cudaMemcpyDeviceToHost, c->st));
+        if (v) CU(cudaMemcpyAsync(v, st + 16 * n, 8 * n, cudaMemcpyDeviceToHost, c->st));
+        if (f) CU(cudaMemcpyAsync(f, st + 24 * n, 8 * n, cudaMemcpyDeviceToHost, c->st));
+    }
     if (step) *step = c->step;
     return dpd_internal_latched(c);
 }

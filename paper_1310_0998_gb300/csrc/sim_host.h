@@ -35,6 +35,7 @@ struct dpd_ctx {
     bool sorted_canonical = false;  // S / cstart hold the canonical positions
     double *h_pin = nullptr;        // small pinned staging (thermo, scalars)
     void *obs = nullptr;            // observables scratch (observables.cu)
+    void *stage = nullptr;          // 32 B/bead staging for host state transfers
 };
 
 int dpd_internal_latched(dpd_ctx *c);

@@ -117,7 +117,7 @@ __device__ void scan_decoupled(const Sys &d, int nblocks)
 template <int B>
 __device__ __forceinline__ void scatter_one(const Sys &d, int k)
 {
-    const float4 xv = d.U_xv[k];
+    const uint4 xv = d.U_xv[k];
     const uint32_t id = d.U_id[k], rank = d.U_rank[k];
     const int c = cell_of<B>(d, cell_coord(d, xv.x), cell_coord(d, xv.y));
     const uint32_t dst = d.cstart[c] + rank;
@@ -127,20 +127,11 @@ __device__ __forceinline__ void scatter_one(const Sys &d, int k)
     d.slot[id] = dst;
 }
 
-// Bin an uploaded/initial state held in U (wrap, check, rank).
+// Bin a state held in U (uploaded or initial): rank of each bead in its cell.
 template <int B>
 __device__ __forceinline__ void bin_one(const Sys &d, int k)
 {
-    float4 xv = d.U_xv[k];
-    if (!(isfinite(xv.x) && isfinite(xv.y) && isfinite(xv.z) && isfinite(xv.w))) {
-        set_err(d, ERR_NONFINITE);
-        xv = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    xv.x = xv.x - d.L * floorf(xv.x / d.L);
-    xv.y = xv.y - d.L * floorf(xv.y / d.L);
-    if (!(xv.x >= 0.f && xv.x < d.L)) xv.x = 0.f;
-    if (!(xv.y >= 0.f && xv.y < d.L)) xv.y = 0.f;
-    d.U_xv[k] = xv;
+    const uint4 xv = d.U_xv[k];
     const int c = cell_of<B>(d, cell_coord(d, xv.x), cell_coord(d, xv.y));
     d.U_rank[k] = atomicAdd(&d.counts[c], 1u);
 }
@@ -152,14 +143,14 @@ struct Thermo3 { float ke, px, py; };
 // bond + propulsion (partner through slot[id ^ 1]), drag, the two half kicks
 // and the drift, canonical output, binning of the new position.
 template <int B>
-__device__ __forceinline__ void integrate_bead(const Sys &d, int g, float4 xv, uint32_t id, float fx,
-                                               float fy, int flags, Thermo3 &th)
+__device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, uint32_t id, float fx, float fy,
+                                               int flags, Thermo3 &th)
 {
     const uint32_t ps = d.slot[id ^ 1u];
     if (ps < (uint32_t)d.n) {
-        const float4 xp = d.S_xv[ps];
-        const float dx = minimg(xv.x, xp.x, d.L, d.halfL);
-        const float dy = minimg(xv.y, xp.y, d.L, d.halfL);
+        const uint4 xp = d.S_xv[ps];
+        const float dx = mdiff(d, xv.x, xp.x);
+        const float dy = mdiff(d, xv.y, xp.y);
         const float r2 = dx * dx + dy * dy;
         if (r2 > 0.f) {
             const float r = sqrtf(r2);
@@ -173,36 +164,35 @@ __device__ __forceinline__ void integrate_bead(const Sys &d, int g, float4 xv, u
     } else {
         set_err(d, ERR_INTERNAL);
     }
-    fx -= d.zeta * xv.z;
-    fy -= d.zeta * xv.w;
-    float vx = xv.z, vy = xv.w;
+    float vx = vbits(xv.z), vy = vbits(xv.w);
+    fx -= d.zeta * vx;
+    fy -= d.zeta * vy;
     if (!(flags & F_FIRST)) { vx += d.hdtm * fx; vy += d.hdtm * fy; }
     th.ke += vx * vx + vy * vy;
     th.px += vx;
     th.py += vy;
     if (flags & F_FINAL) {
-        d.C_xv[id] = make_float4(xv.x, xv.y, vx, vy);
+        d.C_xv[id] = make_uint4(xv.x, xv.y, fbits(vx), fbits(vy));
         d.C_f[id] = make_float2(fx, fy);
     }
     if (flags & F_ADVANCE) {
         vx += d.hdtm * fx;
         vy += d.hdtm * fy;
         const float ddx = d.dt * vx, ddy = d.dt * vy;
-        float nx, ny;
-        if (isfinite(ddx) && isfinite(ddy) && fabsf(ddx) < d.halfL && fabsf(ddy) < d.halfL) {
-            nx = wrap_add(xv.x, ddx, d.L);
-            ny = wrap_add(xv.y, ddy, d.L);
+        uint32_t nx = xv.x, ny = xv.y;
+        if (fabsf(ddx) < 0.25f * d.L && fabsf(ddy) < 0.25f * d.L) {   // false for NaN too
+            nx = fx_add(d, xv.x, ddx);
+            ny = fx_add(d, xv.y, ddy);
         } else {
             set_err(d, ERR_NONFINITE);
-            nx = 0.f; ny = 0.f; vx = 0.f; vy = 0.f;
+            vx = 0.f; vy = 0.f;
         }
         const int c = cell_of<B>(d, cell_coord(d, nx), cell_coord(d, ny));
         d.U_rank[g] = atomicAdd(&d.counts[c], 1u);
-        d.U_xv[g] = make_float4(nx, ny, vx, vy);
+        d.U_xv[g] = make_uint4(nx, ny, fbits(vx), fbits(vy));
         d.U_id[g] = id;
     }
 }
-
 
 // ------------------------------------------------------------ force tile ----
 // Shared-memory plan of one tile (B x B owned cells + one-cell halo).
@@ -270,9 +260,10 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const int tw = min(B, d.nc - x0), th_ = min(B, d.nc - y0);
     const int base = y0 * d.nc + x0 * th_;
     const int nh = 2 * (tw + 2) + 2 * th_;
-    const float ox = ((float)x0 + 0.5f * (float)tw) * d.cs;
-    const float oy = ((float)y0 + 0.5f * (float)th_) * d.cs;
-    const float oxL = ox - d.L, oyL = oy - d.L;
+    // tile-local frame: origin at the tile's centre in fixed
+    // point, offsets formed exactly in 64-bit integers, then one rounding
+    const long long oX = (long long)(((unsigned long long)(2 * x0 + tw) << 31) / (unsigned)d.nc);
+    const long long oY = (long long)(((unsigned long long)(2 * y0 + th_) << 31) / (unsigned)d.nc);
     const uint32_t n = (uint32_t)d.n;
     const long long step = *d.step;
     const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
@@ -331,9 +322,9 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     if (total <= cap) {
         // ---- stage owned + halo beads in shared memory (tile-local frame)
         for (int k = tid; k < n_own; k += NT) {
-            const float4 xv = d.S_xv[g0 + k];
-            s_pos[k] = make_float2(xv.x - ox, xv.y - oy);
-            s_vel[k] = make_float2(xv.z, xv.w);
+            const uint4 xv = d.S_xv[g0 + k];
+            s_pos[k] = make_float2((float)((long long)xv.x - oX) * d.ulen, (float)((long long)xv.y - oY) * d.ulen);
+            s_vel[k] = make_float2(vbits(xv.z), vbits(xv.w));
             s_id[k] = d.S_id[g0 + k];
             s_fx[k] = 0.f;
             s_fy[k] = 0.f;
@@ -350,11 +341,13 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             }
             const int h = lo;
             const uint32_t gsrc = (uint32_t)s_hg[h] + (uint32_t)(k - s_hbeg[h]);
-            const float4 xv = d.S_xv[min(gsrc, n - 1)];
-            const float px = s_hsx[h] < 0 ? (xv.x - d.L) - ox : (s_hsx[h] > 0 ? xv.x - oxL : xv.x - ox);
-            const float py = s_hsy[h] < 0 ? (xv.y - d.L) - oy : (s_hsy[h] > 0 ? xv.y - oyL : xv.y - oy);
-            s_pos[k] = make_float2(px, py);
-            s_vel[k] = make_float2(xv.z, xv.w);
+            const uint4 xv = d.S_xv[min(gsrc, n - 1)];
+            // a halo cell reached across the periodic boundary is the image
+            // shifted by -L (s = -1) or +L (s = +1): 2^32 fixed-point units
+            const long long px = (long long)xv.x + ((long long)s_hsx[h] << 32) - oX;
+            const long long py = (long long)xv.y + ((long long)s_hsy[h] << 32) - oY;
+            s_pos[k] = make_float2((float)px * d.ulen, (float)py * d.ulen);
+            s_vel[k] = make_float2(vbits(xv.z), vbits(xv.w));
             s_id[k] = d.S_id[min(gsrc, n - 1)];
         }
         __syncthreads();
@@ -420,7 +413,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         // ---- integrate owned beads
         for (int k = tid; k < n_own; k += NT) {
             const int g = (int)g0 + k;
-            const float4 xv = d.S_xv[g];
+            const uint4 xv = d.S_xv[g];
             const uint32_t id = s_id[k];
             if (COUNT && d.pcnt) d.pcnt[id] = s_cnt[k];
             integrate_bead<B>(d, g, xv, id, s_fx[k], s_fy[k], flags, th);
@@ -430,7 +423,8 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         if (tid == 0) atomicAdd(d.ovf, 1ull);
         for (int k = tid; k < n_own; k += NT) {
             const int g = (int)g0 + k;
-            const float4 xv = d.S_xv[g];
+            const uint4 xv = d.S_xv[g];
+            const float vix = vbits(xv.z), viy = vbits(xv.w);
             const uint32_t idi = d.S_id[g], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
             const int cx = cell_coord(d, xv.x), cy = cell_coord(d, xv.y);
             float fx = 0.f, fy = 0.f;
@@ -446,14 +440,14 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
                         if (q == (uint32_t)g) continue;
                         const uint32_t idj = d.S_id[q];
                         if (idj == pid) continue;
-                        const float4 xj = d.S_xv[q];
-                        const float dx = minimg(xv.x, xj.x, d.L, d.halfL);
-                        const float dy = minimg(xv.y, xj.y, d.L, d.halfL);
+                        const uint4 xj = d.S_xv[q];
+                        const float dx = mdiff(d, xv.x, xj.x);
+                        const float dy = mdiff(d, xv.y, xj.y);
                         const float r2 = dx * dx + dy * dy;
                         if (r2 < d.rc2 && r2 > 0.f) {
                             float ex, ey;
-                            const float F = dpd_pair_scalar(d, dx, dy, xv.z - xj.z, xv.w - xj.w, idi, idj, s_lo,
-                                                            s_hi, r2, ex, ey);
+                            const float F = dpd_pair_scalar(d, dx, dy, vix - vbits(xj.z), viy - vbits(xj.w), idi,
+                                                            idj, s_lo, s_hi, r2, ex, ey);
                             fx += F * ex;
                             fy += F * ey;
                             if (COUNT) ++cnt;

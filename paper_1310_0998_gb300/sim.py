@@ -38,25 +38,25 @@ class Sim:
         self._h = h
 
     # -------------------------------------------------------------- state
-    def set_state(self, xv, f=None, step: int = 0):
-        """xv: [N,4] (x, y, vx, vy) float32, id order; numpy (host) or a CUDA
-        tensor (device).  f: [N,2] forces of that state or None (set-up)."""
-        if hasattr(xv, "is_cuda"):
+    def set_state(self, x, v, f=None, step: int = 0):
+        """x: [N,2] float64 positions, v: [N,2] float32 velocities, f: [N,2]
+        float32 forces of that state or None (set-up force); id order; numpy
+        arrays (host) or CUDA tensors (device)."""
+        if hasattr(x, "is_cuda"):
             import torch
             torch.cuda.current_stream().synchronize()
         else:
-            xv = np.ascontiguousarray(xv, np.float32)
+            x = np.ascontiguousarray(x, np.float64)
+            v = np.ascontiguousarray(v, np.float32)
             if f is not None:
                 f = np.ascontiguousarray(f, np.float32)
-        assert tuple(xv.shape) == (self.n, 4)
-        check(self._lib.dpd_set_state(self._h, ptr(xv), ptr(f), int(step), where(xv)), "dpd_set_state")
+        assert tuple(x.shape) == (self.n, 2) and tuple(v.shape) == (self.n, 2)
+        check(self._lib.dpd_set_state(self._h, ptr(x), ptr(v), ptr(f), int(step), where(x)), "dpd_set_state")
 
     def set_positions(self, x, v=None, step: int = 0):
-        xv = np.zeros((self.n, 4), np.float32)
-        xv[:, :2] = x
-        if v is not None:
-            xv[:, 2:] = v
-        self.set_state(xv, None, step)
+        if v is None:
+            v = np.zeros((self.n, 2), np.float32)
+        self.set_state(x, v, None, step)
 
     def init_random(self, seed: int = 0):
         check(self._lib.dpd_init_random(self._h, int(seed)), "dpd_init_random")
@@ -67,14 +67,16 @@ class Sim:
     def sync(self):
         check(self._lib.dpd_sync(self._h), "dpd_sync")
 
-    def get_state(self, out_xv=None, out_f=None):
-        """Canonical (xv [N,4], f [N,2], step); host numpy unless CUDA
-        tensors are given as outputs."""
-        xv = out_xv if out_xv is not None else np.empty((self.n, 4), np.float32)
+    def get_state(self, out_x=None, out_v=None, out_f=None):
+        """Canonical (x [N,2] float64, v [N,2] float32, f [N,2] float32, step);
+        host numpy unless CUDA tensors are passed as outputs."""
+        x = out_x if out_x is not None else np.empty((self.n, 2), np.float64)
+        v = out_v if out_v is not None else np.empty((self.n, 2), np.float32)
         f = out_f if out_f is not None else np.empty((self.n, 2), np.float32)
         s = ctypes.c_int64()
-        check(self._lib.dpd_get_state(self._h, ptr(xv), ptr(f), ctypes.byref(s), where(xv)), "dpd_get_state")
-        return xv, f, s.value
+        check(self._lib.dpd_get_state(self._h, ptr(x), ptr(v), ptr(f), ctypes.byref(s), where(x)),
+              "dpd_get_state")
+        return x, v, f, s.value
 
     # -------------------------------------------------------- observables
     def kinetic_energy(self) -> float:

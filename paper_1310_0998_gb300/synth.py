@@ -7,8 +7,9 @@ same bits.  numpy only.
 Initial condition (Sec. 5 of arXiv:1310.0998): agents at uniformly random
 centres and uniformly random orientations, every velocity zero.  Agent k is
 beads 2k (head) and 2k+1 (tail), placed at centre +/- (r0/2)(cos t, sin t) and
-wrapped into [0, L).  Positions are returned in FP32 (the GPU state type); the
-oracle reads the same FP32 values as FP64.
+wrapped into [0, L).  Positions are returned as float64 values on the grid
+x = X L / 2^32 with integer X (the simulator's fixed-point state holds them
+exactly, so both sides start from the same bits); velocities are float32.
 
 Workloads (seed 0 unless stated), in BASELINE units (r_c = 1, m = 1):
   C1  L=32, 512 dimers, a=25, gamma=4.5, kBT=1, kappa=100, r0=0.5, f_p=1,
@@ -41,9 +42,20 @@ def dimers_for_area_fraction(phi: float, L: float) -> int:
     return int(round(2.0 * phi * L * L))
 
 
+def on_grid(x, L: float):
+    """Round positions onto the fixed-point grid X L / 2^32, X in [0, 2^32).
+    L must have at most 21 significant bits so that X L / 2^32 is exact."""
+    L = float(L)
+    u = L / 2.0 ** 32
+    X = np.rint(np.mod(np.asarray(x, np.float64), L) / u).astype(np.int64) % (1 << 32)
+    g = X.astype(np.float64) * u
+    assert np.all(g / u == X), "L has too many significant bits for an exact grid"
+    return g
+
+
 def dimers(n_dimers: int, L: float, r0: float, seed: int = 0):
     """Random centres and orientations, zero velocities.
-    Returns (x [2n,2] float32 in [0,L), v [2n,2] float32 zeros)."""
+    Returns (x [2n,2] float64 on the grid in [0,L), v [2n,2] float32 zeros)."""
     rng = np.random.default_rng(seed)
     c = rng.random((n_dimers, 2)) * L
     t = rng.random(n_dimers) * (2.0 * math.pi)
@@ -51,11 +63,7 @@ def dimers(n_dimers: int, L: float, r0: float, seed: int = 0):
     x = np.empty((2 * n_dimers, 2), np.float64)
     x[0::2] = c + h
     x[1::2] = c - h
-    x = np.mod(x, L)
-    x32 = x.astype(np.float32)
-    x32[x32 >= np.float32(L)] = 0.0
-    v32 = np.zeros_like(x32)
-    return x32, v32
+    return on_grid(x, L), np.zeros((2 * n_dimers, 2), np.float32)
 
 
 def velocities(n_beads: int, scale: float, seed: int = 1):
@@ -65,11 +73,9 @@ def velocities(n_beads: int, scale: float, seed: int = 1):
 
 
 def uniform_beads(n_beads: int, L: float, seed: int = 0):
-    """Beads uniformly in the box (any pairing), FP32."""
+    """Beads uniformly in the box (any pairing), on the grid."""
     rng = np.random.default_rng(seed)
-    x = (rng.random((n_beads, 2)) * L).astype(np.float32)
-    x[x >= np.float32(L)] = 0.0
-    return x
+    return on_grid(rng.random((n_beads, 2)) * L, L)
 
 
 def ensemble_points(R: int, seed: int = 0):
@@ -78,7 +84,7 @@ def ensemble_points(R: int, seed: int = 0):
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(R):
-        L = float(rng.uniform(32.0, 192.0))
+        L = round(float(rng.uniform(32.0, 192.0)) * 256.0) / 256.0   # exact fixed-point grid
         phi = float(rng.uniform(0.05, 0.6))
         gamma = float(math.exp(rng.uniform(math.log(0.5), math.log(50.0))))
         zeta = float(math.exp(rng.uniform(math.log(0.005), math.log(2.0))))

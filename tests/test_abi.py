@@ -35,7 +35,7 @@ def test_validation_without_gpu():
     L = _lib.lib()
     h = ctypes.c_void_p()
     bad = [
-        make_params(2.0, 10),               # L < 3 r_c
+        make_params(2.9, 10),               # L < 3 r_c
         make_params(10.0, 9),               # odd bead count
         make_params(10.0, 0),
         make_params(10.0, 10, dt=0.0),
@@ -54,7 +54,7 @@ def test_validation_without_gpu():
 
 
 def test_cell_side_rule():
-    """n_c = floor(L / (r_c + 2^-20 L)): cells strictly wider than r_c."""
+    """n_c = floor(L / r_c): cells at least r_c wide."""
     import math
-    for L, rc, nc in [(32.0, 1.0, 31), (1024.0, 1.0, 1023), (100.0, 0.5, 199), (3.0, 1.0, 2), (3.1, 1.0, 3)]:
-        assert math.floor(L / (rc + 2.0 ** -20 * L)) == nc
+    for L, rc, nc in [(32.0, 1.0, 32), (1024.0, 1.0, 1024), (100.0, 0.5, 200), (3.0, 1.0, 3), (2.9, 1.0, 2)]:
+        assert math.floor(L / rc) == nc

@@ -253,34 +253,34 @@ def test_cell_list_variant_matches_all_pairs(orc):
 
 
 def test_cell_rule_stencil_is_sufficient(orc):
-    """With n_c = floor(L / (r_c + 2^-20 L)) cells per side and the FP32
-    binning rule, every interacting pair sits in the same or an adjacent cell
-    (periodically), so a 3x3 stencil finds all pairs."""
-    for L, seed in [(3.0, 0), (7.0, 1), (32.0, 2), (1024.0, 3)]:
-        nc = int(math.floor(L / (1.0 + 2.0 ** -20 * L)))
+    """With n_c = floor(L / r_c) cells per side and bead x in cell
+    floor(x n_c / L) (exact on the fixed-point grid), every interacting pair
+    sits in the same or an adjacent cell (periodically), so a 3 x 3 stencil
+    finds all pairs; the counts cover every bead once."""
+    for L, seed in [(3.0, 0), (7.0, 1), (32.0, 2), (1024.0, 3), (100.0, 4)]:
+        rc = 0.5 if L == 100.0 else 1.0
+        nc = int(math.floor(L / rc))
         rng = np.random.default_rng(seed)
         n = 400
-        x = (rng.random((n, 2)) * L).astype(np.float32)
-        # put pairs straddling cell edges at just under r_c
-        edges = (np.arange(min(nc, 50)) * np.float32(L / nc)).astype(np.float32)
-        k = len(edges)
-        x[:k, 0] = edges + np.float32(1e-6 * L)
-        x[k:2 * k, 0] = np.mod(x[:k, 0] + np.float32(0.9999), np.float32(L))
+        x = rng.random((n, 2)) * L
+        # pairs straddling cell edges at just under r_c
+        k = min(nc, 50)
+        edges = np.arange(k) * (L / nc)
+        x[:k, 0] = edges + 1e-9 * L
+        x[k:2 * k, 0] = x[:k, 0] + rc * (1 - 1e-7)
         x[k:2 * k, 1] = x[:k, 1]
-        x[x >= np.float32(L)] = 0
+        x = synth.on_grid(x, L)
         cnt = orc.cell_counts(x, L, nc)
         assert cnt.sum() == n
-        inv = np.float32(nc) / np.float32(L)
-        cx = np.minimum(nc - 1, (x[:, 0] * inv).astype(np.int64))
-        cy = np.minimum(nc - 1, (x[:, 1] * inv).astype(np.int64))
-        cs = L / nc
-        # each bead lies in its cell up to FP32 rounding of the product
-        assert np.all(x[:, 0] >= cx * cs - 1e-6 * L) and np.all(x[:, 0] <= (cx + 1) * cs + 1e-6 * L)
-        xd = x.astype(np.float64)
-        d = xd[:, None, :] - xd[None, :, :]
+        X = np.rint(x / L * 2.0 ** 32).astype(np.int64)
+        cx = (X[:, 0] * nc) >> 32
+        cy = (X[:, 1] * nc) >> 32
+        assert np.all(cx * (L / nc) <= x[:, 0] + 1e-12) and np.all(x[:, 0] < (cx + 1) * (L / nc) + 1e-12)
+        np.testing.assert_array_equal(cnt, np.histogram2d(cy, cx, bins=nc, range=[[0, nc], [0, nc]])[0])
+        d = x[:, None, :] - x[None, :, :]
         d -= L * np.rint(d / L)
         r2 = (d ** 2).sum(-1)
-        ii, jj = np.nonzero(np.triu(r2 < 1.0, 1))
+        ii, jj = np.nonzero(np.triu(r2 < rc * rc, 1))
         ddx = np.abs(cx[ii] - cx[jj]); ddx = np.minimum(ddx, nc - ddx)
         ddy = np.abs(cy[ii] - cy[jj]); ddy = np.minimum(ddy, nc - ddy)
         assert ddx.max(initial=0) <= 1 and ddy.max(initial=0) <= 1
