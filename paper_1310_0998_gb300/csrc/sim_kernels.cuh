@@ -200,7 +200,7 @@ template <int B>
 struct TilePlan {
     static constexpr int NCL = (B + 2) * (B + 2);   // local cell table
     static constexpr int NH = 4 * B + 4;            // halo cells
-    static constexpr int NINT = 2 * NCL + 5 * (NH + 1) + 8;
+    static constexpr int NINT = 2 * NCL + 5 * (NH + 1) + 2 * (B + 2) + 8;
     static __host__ __device__ size_t red_off() { return ((size_t)NINT * 4 + 7) & ~size_t(7); }
     static __host__ __device__ size_t bead_off(int nthreads)
     {
@@ -245,7 +245,9 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     int *s_hcnt = s_hbeg + (TP::NH + 1);
     int *s_hsx = s_hcnt + (TP::NH + 1);
     int *s_hsy = s_hsx + (TP::NH + 1);
-    int *s_sc = s_hsy + (TP::NH + 1);
+    uint32_t *s_crx = (uint32_t *)(s_hsy + (TP::NH + 1));   // cell corners (fixed point)
+    uint32_t *s_cry = s_crx + (B + 2);
+    int *s_sc = (int *)(s_cry + (B + 2));
     const int cap = d.cap;
     float2 *s_pos = (float2 *)(smem + TP::bead_off(NT));
     float2 *s_vel = s_pos + cap;
@@ -260,10 +262,11 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const int tw = min(B, d.nc - x0), th_ = min(B, d.nc - y0);
     const int base = y0 * d.nc + x0 * th_;
     const int nh = 2 * (tw + 2) + 2 * th_;
-    // tile-local frame: origin at the tile's centre in fixed
-    // point, offsets formed exactly in 64-bit integers, then one rounding
-    const long long oX = (long long)(((unsigned long long)(2 * x0 + tw) << 31) / (unsigned)d.nc);
-    const long long oY = (long long)(((unsigned long long)(2 * y0 + th_) << 31) / (unsigned)d.nc);
+    // Each staged bead keeps its offset from its own cell's corner
+    // C(c) = ceil(c 2^32 / nc) (exact integer difference, one rounding), so
+    // the precision of a pair separation does not depend on the tile size or
+    // on L; the separation to a bead in the cell (dcx, dcy) away is
+    // off_i - off_j - (dcx, dcy) cs up to one fixed-point unit.
     const uint32_t n = (uint32_t)d.n;
     const long long step = *d.step;
     const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
@@ -273,6 +276,13 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const uint32_t g1 = max(g0, min(d.cstart[base + tw * th_], n));
     const int n_own = (int)(g1 - g0);
 
+    for (int c = tid; c < 2 * (B + 2); c += NT) {
+        const int q = c < B + 2 ? c : c - (B + 2);
+        int cc = (c < B + 2 ? x0 : y0) + q - 1;
+        cc += cc < 0 ? d.nc : (cc >= d.nc ? -d.nc : 0);
+        const uint32_t corner = (uint32_t)((((unsigned long long)cc << 32) + (unsigned)d.nc - 1ull) / (unsigned)d.nc);
+        if (c < B + 2) s_crx[q] = corner; else s_cry[q] = corner;
+    }
     // owned cell table
     for (int c = tid; c < tw * th_; c += NT) {
         const int ly = c / tw, lx = c - ly * tw;
@@ -323,14 +333,15 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         // ---- stage owned + halo beads in shared memory (tile-local frame)
         for (int k = tid; k < n_own; k += NT) {
             const uint4 xv = d.S_xv[g0 + k];
-            s_pos[k] = make_float2((float)((long long)xv.x - oX) * d.ulen, (float)((long long)xv.y - oY) * d.ulen);
+            const int lx = min(max(cell_coord(d, xv.x) - x0, 0), tw - 1);
+            const int ly = min(max(cell_coord(d, xv.y) - y0, 0), th_ - 1);
+            s_pos[k] = make_float2((float)(int)(xv.x - s_crx[lx + 1]) * d.ulen,
+                                   (float)(int)(xv.y - s_cry[ly + 1]) * d.ulen);
             s_vel[k] = make_float2(vbits(xv.z), vbits(xv.w));
             s_id[k] = d.S_id[g0 + k];
             s_fx[k] = 0.f;
             s_fy[k] = 0.f;
             if (COUNT) s_cnt[k] = 0u;
-            const int lx = min(max(cell_coord(d, xv.x) - x0, 0), tw - 1);
-            const int ly = min(max(cell_coord(d, xv.y) - y0, 0), th_ - 1);
             s_lc[k] = (unsigned char)(lx | (ly << 4));
         }
         for (int k = n_own + tid; k < total; k += NT) {
@@ -342,11 +353,14 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             const int h = lo;
             const uint32_t gsrc = (uint32_t)s_hg[h] + (uint32_t)(k - s_hbeg[h]);
             const uint4 xv = d.S_xv[min(gsrc, n - 1)];
-            // a halo cell reached across the periodic boundary is the image
-            // shifted by -L (s = -1) or +L (s = +1): 2^32 fixed-point units
-            const long long px = (long long)xv.x + ((long long)s_hsx[h] << 32) - oX;
-            const long long py = (long long)xv.y + ((long long)s_hsy[h] << 32) - oY;
-            s_pos[k] = make_float2((float)px * d.ulen, (float)py * d.ulen);
+            int hx, hy;   // local cell of halo cell h (perimeter order)
+            if (h < tw + 2) { hx = h - 1; hy = -1; }
+            else if (h < 2 * (tw + 2)) { hx = h - (tw + 2) - 1; hy = th_; }
+            else if (h < 2 * (tw + 2) + th_) { hx = -1; hy = h - 2 * (tw + 2); }
+            else { hx = tw; hy = h - 2 * (tw + 2) - th_; }
+            // the offset from the cell corner is the same for a periodic image
+            s_pos[k] = make_float2((float)(int)(xv.x - s_crx[hx + 1]) * d.ulen,
+                                   (float)(int)(xv.y - s_cry[hy + 1]) * d.ulen);
             s_vel[k] = make_float2(vbits(xv.z), vbits(xv.w));
             s_id[k] = d.S_id[min(gsrc, n - 1)];
         }
@@ -354,7 +368,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
 
         // ---- pair forces
         for (int k = tid; k < n_own; k += NT) {
-            const float2 pi = s_pos[k], vi = s_vel[k];
+            const float2 oi = s_pos[k], vi = s_vel[k];
             const uint32_t idi = s_id[k], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
             const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
             float fx = 0.f, fy = 0.f;
@@ -378,13 +392,14 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
                 const bool owned = (nlx >= 0 && nlx < tw && nly >= 0 && nly < th_);
                 if (nb >= 5 && owned) continue;    // the other bead's forward sweep takes it
                 const bool newton = owned;
+                const float pix = oi.x - (float)ox_ * d.cs, piy = oi.y - (float)oy_ * d.cs;
                 const int lc = (nly + 1) * (B + 2) + nlx + 1;
                 int j = s_cbeg[lc];
                 const int je = j + s_ccnt[lc];
                 if (nb == 0) j = k + 1;
                 for (; j < je; ++j) {
                     const float2 pj = s_pos[j];
-                    const float dx = pi.x - pj.x, dy = pi.y - pj.y;
+                    const float dx = pix - pj.x, dy = piy - pj.y;
                     const float r2 = dx * dx + dy * dy;
                     if (r2 < d.rc2 && r2 > 0.f) {
                         const uint32_t idj = s_id[j];

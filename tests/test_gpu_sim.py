@@ -201,7 +201,8 @@ def test_single_dimer_drift(Sim):
     d = minimg(x[0] - x[1], L)
     n = d / np.linalg.norm(d)
     np.testing.assert_allclose(vg[0] @ n, u, rtol=1e-5)
-    np.testing.assert_allclose(vg[1], vg[0], atol=1e-5)
+    # both beads move together up to FP32 rounding over 3000 steps
+    np.testing.assert_allclose(vg[1], vg[0], atol=1e-5 * max(1.0, abs(u)))
 
 
 def test_init_random_initial_condition(Sim):
