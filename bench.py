@@ -159,6 +159,8 @@ def main():
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue")
+    ap.add_argument("--tile", type=int, default=0, help="cell-block side: 0 default, 4, 8, 16")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = CONFIGS[args.config]
@@ -182,7 +184,7 @@ def main():
     x, v = synth.dimers(nb // 2, L, PHYS["r0"], seed=rank)
     sim = Sim(L, nb, stream=stream.cuda_stream, seed=rank, a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"],
               rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"],
-              dt=PHYS["dt"], mass=PHYS["mass"])
+              dt=PHYS["dt"], mass=PHYS["mass"], variant=args.variant, tile=args.tile)
     sim.set_positions(x, v)
     for _ in range(args.warmup):
         sim.step(1)
@@ -262,7 +264,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "beads": nb, "L": L, "bead_density": nb / L / L,
-                   "tile": info.tile, "l2": "512 MiB write+read flush between timed steps",
+                   "tile": info.tile, "variant": info.variant,
+                   "l2": "512 MiB write+read flush between timed steps",
                    "pairs_per_bead": npairs / nb, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "force_integrate", "achieved": alu_ach / 1e12,
                      "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": None,

@@ -44,6 +44,7 @@ struct Sys {
     int nc, ntx, n, ncells;
     float rc2, inv_rc, a, gamma, sig_r, kbond, r0, fp, zeta, dt, hdtm;
     uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];   // Philox round keys key + r * (Weyl increments)
     int noise, excl, cap;
     uint4 *S_xv;
     uint32_t *S_id;
@@ -80,6 +81,21 @@ __device__ __forceinline__ void philox10(uint32_t &c0, uint32_t &c1, uint32_t &c
     }
 }
 
+// Same bijection with the ten round keys precomputed (k + r W per round).
+__device__ __forceinline__ void philox10_rk(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                            const uint32_t *rk0, const uint32_t *rk1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        c0 = hi1 ^ c1 ^ rk0[r];
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ rk1[r];
+        c3 = lo0;
+    }
+}
+
 // Random factor of the pair (i, j) at step s: F_R = sig_r * w * noise.
 // Uniform: the odd integer 2 (w0 >> 8) + 1 - 2^24 (|.| < 2^24, exact in FP32);
 // sig_r carries sqrt(2 gamma kBT / dt) * sqrt(3) * 2^-24.
@@ -88,8 +104,10 @@ __device__ __forceinline__ float pair_noise(const Sys &d, uint32_t ia, uint32_t 
                                             uint32_t s_hi)
 {
     uint32_t c0 = min(ia, ib), c1 = max(ia, ib), c2 = s_lo, c3 = s_hi;
-    philox10(c0, c1, c2, c3, d.key0, d.key1);
-    if (d.noise == 0) return (float)((int)((c0 >> 8) * 2u + 1u) - (1 << 24));
+    philox10_rk(c0, c1, c2, c3, d.rk0, d.rk1);
+    // 2 (w0 >> 8) + 1 - 2^24, formed exactly in FP32 (every term is an
+    // integer below 2^25 in magnitude with at most 24 significant bits)
+    if (d.noise == 0) return fmaf((float)(c0 >> 8), 2.0f, 1.0f - 16777216.0f);
     const float u1 = ((float)(c0 >> 8) + 0.5f) * 5.9604644775390625e-08f;
     const float u2 = ((float)(c1 >> 8) + 0.5f) * 5.9604644775390625e-08f;
     return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);

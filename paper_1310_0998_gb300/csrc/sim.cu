@@ -131,12 +131,12 @@ __global__ void k_kick_bin(Sys d)
     thermo_flush(d, th, s_red);
 }
 
-template <int B, bool COUNT>
-__global__ void __launch_bounds__(256) k_force(Sys d, int flags)
+template <int B, bool COUNT, int VAR>
+__global__ void __launch_bounds__(TILE_THREADS, 6) k_force(Sys d, int flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Thermo3 th{0.f, 0.f, 0.f};
-    force_tile<B, COUNT>(d, blockIdx.x, flags, smem, th);
+    force_tile<B, COUNT, VAR>(d, blockIdx.x, flags, smem, th);
     if (flags & (F_ADVANCE | F_FINAL)) {
         __syncthreads();
         thermo_flush(d, th, (double *)(smem + TilePlan<B>::red_off()));
@@ -211,6 +211,10 @@ void fill_physics(Sys &d, const dpd_params *p)
     d.hdtm = (float)(0.5 * p->dt / p->mass);
     d.key0 = (uint32_t)(p->seed & 0xffffffffull);
     d.key1 = (uint32_t)(p->seed >> 32) ^ p->replica;
+    for (int r = 0; r < 10; ++r) {
+        d.rk0[r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
+        d.rk1[r] = d.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     d.noise = p->noise;
     d.excl = p->exclude_bonded ? 1 : 0;
 }
@@ -236,62 +240,78 @@ int tile_capacity(const dpd_params *p, int B)
     const double cs = p->L / nc;
     const double rho = (double)p->n_beads / (p->L * p->L);
     const double mean = rho * ((B + 2) * cs) * ((B + 2) * cs);
-    int cap = (int)std::ceil(4.0 * mean + 96.0);
+    // mean staged population plus a wide margin for density fluctuations;
+    // a tile above it takes the (slower, exact) global-memory path
+    int cap = (int)std::ceil(1.5 * mean + 8.0 * std::sqrt(mean) + 64.0);
     cap = (cap + 31) & ~31;
-    return std::max(cap, 256);
+    return std::min(std::max(cap, 256), 4096);   // queue entries pack bead slots in 12 bits
 }
 
-size_t force_smem(int B, int cap)
+size_t force_smem(int B, int cap, bool count)
 {
     switch (B) {
-        case 4: return TilePlan<4>::bytes(cap, 256);
-        case 8: return TilePlan<8>::bytes(cap, 256);
-        default: return TilePlan<16>::bytes(cap, 256);
+        case 4: return TilePlan<4>::bytes(cap, TILE_THREADS, count);
+        case 8: return TilePlan<8>::bytes(cap, TILE_THREADS, count);
+        default: return TilePlan<16>::bytes(cap, TILE_THREADS, count);
     }
 }
 
 template <int B>
-static int set_force_attrs(size_t smem)
+static int set_force_attrs(int cap)
 {
-    CU(cudaFuncSetAttribute(k_force<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CU(cudaFuncSetAttribute(k_force<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int s0 = (int)TilePlan<B>::bytes(cap, TILE_THREADS, false), s1 = (int)TilePlan<B>::bytes(cap, TILE_THREADS, true);
+    CU(cudaFuncSetAttribute(k_force<B, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
+    CU(cudaFuncSetAttribute(k_force<B, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+    CU(cudaFuncSetAttribute(k_force<B, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
+    CU(cudaFuncSetAttribute(k_force<B, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
     return DPD_OK;
 }
 
-template <int B>
-static void launch_iteration_t(const Sys &d, cudaStream_t st, int nscan, size_t smem, int flags, bool count)
+int set_force_smem(int B, int cap)
+{
+    return B == 4 ? set_force_attrs<4>(cap) : B == 8 ? set_force_attrs<8>(cap) : set_force_attrs<16>(cap);
+}
+
+template <int B, int VAR>
+static void launch_force_t(const Sys &d, cudaStream_t st, size_t smem, int flags, bool count)
 {
     const int ntiles = d.ntx * d.ntx;
+    if (count) k_force<B, true, VAR><<<ntiles, TILE_THREADS, force_smem(B, d.cap, true), st>>>(d, flags);
+    else k_force<B, false, VAR><<<ntiles, TILE_THREADS, smem, st>>>(d, flags);
+}
+
+void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t smem, int flags, bool count)
+{
+    if (var == 1) {
+        switch (B) {
+            case 4: launch_force_t<4, 1>(d, st, smem, flags, count); break;
+            case 8: launch_force_t<8, 1>(d, st, smem, flags, count); break;
+            default: launch_force_t<16, 1>(d, st, smem, flags, count); break;
+        }
+    } else {
+        switch (B) {
+            case 4: launch_force_t<4, 2>(d, st, smem, flags, count); break;
+            case 8: launch_force_t<8, 2>(d, st, smem, flags, count); break;
+            default: launch_force_t<16, 2>(d, st, smem, flags, count); break;
+        }
+    }
+}
+
+void launch_scatter(const Sys &d, int B, cudaStream_t st)
+{
+    const int g = (d.n + 255) / 256;
+    switch (B) {
+        case 4: k_scatter<4><<<g, 256, 0, st>>>(d); break;
+        case 8: k_scatter<8><<<g, 256, 0, st>>>(d); break;
+        default: k_scatter<16><<<g, 256, 0, st>>>(d); break;
+    }
+}
+
+void launch_iteration(const Sys &d, int B, int var, cudaStream_t st, int nscan, size_t smem, int flags, bool count)
+{
     k_scan<<<nscan, SCAN_NT, 0, st>>>(d, nscan);
-    k_scatter<B><<<(d.n + 255) / 256, 256, 0, st>>>(d);
-    if (count) k_force<B, true><<<ntiles, 256, smem, st>>>(d, flags);
-    else k_force<B, false><<<ntiles, 256, smem, st>>>(d, flags);
-}
-
-void launch_iteration(const Sys &d, int B, cudaStream_t st, int nscan, size_t smem, int flags, bool count)
-{
-    switch (B) {
-        case 4: launch_iteration_t<4>(d, st, nscan, smem, flags, count); break;
-        case 8: launch_iteration_t<8>(d, st, nscan, smem, flags, count); break;
-        default: launch_iteration_t<16>(d, st, nscan, smem, flags, count); break;
-    }
-}
-
-template <int B>
-static void launch_force_only_t(const Sys &d, cudaStream_t st, size_t smem, int flags, bool count)
-{
-    const int ntiles = d.ntx * d.ntx;
-    if (count) k_force<B, true><<<ntiles, 256, smem, st>>>(d, flags);
-    else k_force<B, false><<<ntiles, 256, smem, st>>>(d, flags);
-}
-
-void launch_force_only(const Sys &d, int B, cudaStream_t st, size_t smem, int flags, bool count)
-{
-    switch (B) {
-        case 4: launch_force_only_t<4>(d, st, smem, flags, count); break;
-        case 8: launch_force_only_t<8>(d, st, smem, flags, count); break;
-        default: launch_force_only_t<16>(d, st, smem, flags, count); break;
-    }
+    launch_scatter(d, B, st);
+    launch_force_only(d, B, var, st, smem, flags, count);
 }
 
 void launch_bin(const Sys &d, int B, cudaStream_t st)
@@ -338,7 +358,7 @@ static int capture(dpd_ctx *c, int iters, int last_flags, cudaGraphExec_t *out)
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < iters; ++i)
-        launch_iteration(c->d, c->B, c->st, c->nscan, c->smem, i == iters - 1 ? last_flags : F_ADVANCE, false);
+        launch_iteration(c->d, c->B, c->var, c->st, c->nscan, c->smem, i == iters - 1 ? last_flags : F_ADVANCE, false);
     const cudaError_t e = cudaStreamEndCapture(c->st, &g);
     if (e != cudaSuccess) return cuerr(e);
     const cudaError_t e2 = cudaGraphInstantiate(out, g, 0);
@@ -396,6 +416,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     if (!c) return DPD_ERR_OOM;
     c->p = *p;
     c->B = p->tile ? p->tile : 8;
+    c->var = p->variant ? p->variant : 2;
     if (stream) {
         c->st = (cudaStream_t)stream;
     } else {
@@ -406,10 +427,10 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     fill_geometry(d, p, c->B);
     fill_physics(d, p);
     d.cap = tile_capacity(p, c->B);
-    c->smem = force_smem(c->B, d.cap);
-    if (c->smem > 200 * 1024) {
-        d.cap = (int)((200 * 1024 - force_smem(c->B, 0)) / 33) & ~31;
-        c->smem = force_smem(c->B, d.cap);
+    c->smem = force_smem(c->B, d.cap, false);
+    if (force_smem(c->B, d.cap, true) > 200 * 1024) {
+        d.cap = (int)((200 * 1024 - force_smem(c->B, 0, true)) / 33) & ~31;
+        c->smem = force_smem(c->B, d.cap, false);
     }
     c->nscan = (d.ncells + SCAN_TILE - 1) / SCAN_TILE;
     const size_t n = (size_t)d.n, nce = (size_t)d.ncells;
@@ -454,8 +475,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     d.scan_status = (unsigned long long *)(b + o_ss);
     d.scan_ticket = (unsigned long long *)(b + o_tk);
     if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess ||
-        (rc = (c->B == 4 ? set_force_attrs<4>(c->smem) : c->B == 8 ? set_force_attrs<8>(c->smem)
-                                                              : set_force_attrs<16>(c->smem))) != DPD_OK) {
+        (rc = set_force_smem(c->B, d.cap)) != DPD_OK) {
         dpd_destroy(c);
         return rc ? rc : DPD_ERR_CUDA;
     }
@@ -484,6 +504,7 @@ int dpd_set_params(dpd_ctx *c, const dpd_params *p)
     if (p->n_beads != c->p.n_beads || p->L != c->p.L || p->rc != c->p.rc) return DPD_ERR_STATE;
     const int B = p->tile ? p->tile : 8;
     if (B != c->B) return DPD_ERR_STATE;
+    c->var = p->variant ? p->variant : 2;
     c->p = *p;
     fill_physics(c->d, p);
     free_graphs(c);   // kernel arguments carry the parameters
@@ -495,7 +516,7 @@ static int start_from_U(dpd_ctx *c, long long step)
     // U holds an unbinned state in id order: bin it, then the set-up step.
     launch_bin(c->d, c->B, c->st);
     k_set_step<<<1, 1, 0, c->st>>>(c->d, step - 1);
-    launch_iteration(c->d, c->B, c->st, c->nscan, c->smem, F_FIRST | F_FINAL | F_ADVANCE, false);
+    launch_iteration(c->d, c->B, c->var, c->st, c->nscan, c->smem, F_FIRST | F_FINAL | F_ADVANCE, false);
     CU(cudaGetLastError());
     c->step = step;
     c->have_state = true;
@@ -680,7 +701,7 @@ int dpd_pair_counts(dpd_ctx *c, uint32_t *cnt, uint64_t *total)
     const size_t n = (size_t)c->d.n;
     Sys d = c->d;
     d.pcnt = c->pcnt_buf;
-    launch_force_only(d, c->B, c->st, c->smem, 0, true);
+    launch_force_only(d, c->B, c->var, c->st, c->smem, 0, true);
     CU(cudaGetLastError());
     std::vector<uint32_t> h(n);
     CU(cudaMemcpyAsync(h.data(), c->pcnt_buf, 4 * n, cudaMemcpyDeviceToHost, c->st));
@@ -702,13 +723,9 @@ int dpd_profile_step(dpd_ctx *c, double ms[3])
     CU(cudaEventRecord(ev[0], c->st));
     k_scan<<<c->nscan, SCAN_NT, 0, c->st>>>(d, c->nscan);
     CU(cudaEventRecord(ev[1], c->st));
-    switch (c->B) {
-        case 4: k_scatter<4><<<(d.n + 255) / 256, 256, 0, c->st>>>(d); break;
-        case 8: k_scatter<8><<<(d.n + 255) / 256, 256, 0, c->st>>>(d); break;
-        default: k_scatter<16><<<(d.n + 255) / 256, 256, 0, c->st>>>(d); break;
-    }
+    launch_scatter(d, c->B, c->st);
     CU(cudaEventRecord(ev[2], c->st));
-    launch_force_only(d, c->B, c->st, c->smem, F_ADVANCE | F_FINAL, false);
+    launch_force_only(d, c->B, c->var, c->st, c->smem, F_ADVANCE | F_FINAL, false);
     CU(cudaEventRecord(ev[3], c->st));
     CU(cudaGetLastError());
     c->step += 1;
@@ -734,7 +751,7 @@ int dpd_get_info(dpd_ctx *c, dpd_info *info)
     info->n_cells_side = c->d.nc;
     info->tile = c->B;
     info->n_tiles = c->d.ntx * c->d.ntx;
-    info->variant = 1;
+    info->variant = c->var;
     info->step = c->step;
     info->overflow_tiles = (int64_t)ovf;
     info->device_bytes = (int64_t)c->pool_bytes;

@@ -11,9 +11,11 @@ int validate(const dpd_params *p);
 void fill_physics(Sys &d, const dpd_params *p);
 void fill_geometry(Sys &d, const dpd_params *p, int B);
 int tile_capacity(const dpd_params *p, int B);
-size_t force_smem(int B, int cap);
-void launch_iteration(const Sys &d, int B, cudaStream_t st, int nscan, size_t smem, int flags, bool count);
-void launch_force_only(const Sys &d, int B, cudaStream_t st, size_t smem, int flags, bool count);
+size_t force_smem(int B, int cap, bool count);
+void launch_iteration(const Sys &d, int B, int var, cudaStream_t st, int nscan, size_t smem, int flags, bool count);
+void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t smem, int flags, bool count);
+void launch_scatter(const Sys &d, int B, cudaStream_t st);
+int set_force_smem(int B, int cap);
 void launch_bin(const Sys &d, int B, cudaStream_t st);
 void launch_kick_bin(const Sys &d, int B, cudaStream_t st);
 int host_cell_of(int B, int nc, int cx, int cy);
@@ -24,7 +26,7 @@ struct dpd_ctx {
     dpd::Sys d{};
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    int B = 8, nscan = 1;
+    int B = 8, var = 2, nscan = 1;
     size_t smem = 0;
     void *pool = nullptr;
     size_t pool_bytes = 0;

@@ -196,6 +196,7 @@ __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, ui
 
 // ------------------------------------------------------------ force tile ----
 // Shared-memory plan of one tile (B x B owned cells + one-cell halo).
+constexpr int TILE_THREADS = 128;
 template <int B>
 struct TilePlan {
     static constexpr int NCL = (B + 2) * (B + 2);   // local cell table
@@ -206,9 +207,15 @@ struct TilePlan {
     {
         return (red_off() + sizeof(double) * 3 * (size_t)(nthreads / 32 + 1) + 15) & ~size_t(15);
     }
-    static __host__ __device__ size_t bytes(int cap, int nthreads)
+    // per staged bead: pos 8, vel 8, id 4, fx 4, fy 4, local cell 1 (+ count 4)
+    static __host__ __device__ size_t bead_bytes(bool count) { return count ? 33 : 29; }
+    static __host__ __device__ size_t queue_off(int cap, int nthreads, bool count)
     {
-        return (bead_off(nthreads) + (size_t)cap * (8 + 8 + 4 + 4 + 4 + 4 + 1) + 15) & ~size_t(15);
+        return (bead_off(nthreads) + (size_t)cap * bead_bytes(count) + 15) & ~size_t(15);
+    }
+    static __host__ __device__ size_t bytes(int cap, int nthreads, bool count)
+    {
+        return queue_off(cap, nthreads, count) + sizeof(uint32_t) * 128 * (size_t)(nthreads / 32);
     }
 };
 
@@ -226,6 +233,203 @@ __device__ __forceinline__ float dpd_pair_scalar(const Sys &d, float dx, float d
     return w * (d.a - d.gamma * w * dve + d.sig_r * nz);
 }
 
+
+// Neighbour offsets packed 2 bits per entry (value + 1), entries in the
+// order 0 = own cell, 1-4 ahead (E, NE, N, NW), 5-8 behind (W, SW, S, SE).
+constexpr uint32_t NB_DX = 0x1u | (2u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (0u << 10) | (0u << 12) |
+                           (1u << 14) | (2u << 16);
+constexpr uint32_t NB_DY = 0x1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8) | (1u << 10) | (0u << 12) |
+                           (0u << 14) | (0u << 16);
+
+// Offset of bead i seen from a bead in the cell (dx, dy) away.
+__device__ __forceinline__ float shift_off(float o, int dx, float cs)
+{
+    return dx == 0 ? o : (dx > 0 ? o - cs : o + cs);
+}
+
+// Variant 1: one thread per owned bead walks its candidates and evaluates
+// each interacting pair in place (divergent; kept as the simple reference
+// kernel and for the autotuner).
+template <int B, bool COUNT>
+__device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, int th_, const int *s_cbeg,
+                                             const int *s_ccnt, const float2 *s_pos, const float2 *s_vel,
+                                             const uint32_t *s_id, float *s_fx, float *s_fy, uint32_t *s_cnt,
+                                             const unsigned char *s_lc, uint32_t s_lo, uint32_t s_hi)
+{
+    for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
+        const float2 oi = s_pos[k], vi = s_vel[k];
+        const uint32_t idi = s_id[k], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
+        const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
+        float fx = 0.f, fy = 0.f;
+        uint32_t cnt = 0;
+#pragma unroll 1
+        for (int nb = 0; nb < 9; ++nb) {
+            const int ox_ = (int)((NB_DX >> (2 * nb)) & 3u) - 1, oy_ = (int)((NB_DY >> (2 * nb)) & 3u) - 1;
+            const int nlx = lx + ox_, nly = ly + oy_;
+            const bool owned = (nlx >= 0 && nlx < tw && nly >= 0 && nly < th_);
+            if (nb >= 5 && owned) continue;    // the other bead's forward sweep takes it
+            const bool newton = owned;
+            const float pix = shift_off(oi.x, ox_, d.cs), piy = shift_off(oi.y, oy_, d.cs);
+            const int lc = (nly + 1) * (B + 2) + nlx + 1;
+            int j = s_cbeg[lc];
+            const int je = j + s_ccnt[lc];
+            if (nb == 0) j = k + 1;
+            for (; j < je; ++j) {
+                const float2 pj = s_pos[j];
+                const float dx = pix - pj.x, dy = piy - pj.y;
+                const float r2 = dx * dx + dy * dy;
+                if (r2 < d.rc2 && r2 > 0.f) {
+                    const uint32_t idj = s_id[j];
+                    if (idj == pid) continue;
+                    const float2 vj = s_vel[j];
+                    float ex, ey;
+                    const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, idi, idj, s_lo, s_hi, r2,
+                                                    ex, ey);
+                    fx += F * ex;
+                    fy += F * ey;
+                    if (COUNT) ++cnt;
+                    if (newton) {
+                        atomicAdd(&s_fx[j], -F * ex);
+                        atomicAdd(&s_fy[j], -F * ey);
+                        if (COUNT) atomicAdd(&s_cnt[j], 1u);
+                    }
+                }
+            }
+        }
+        atomicAdd(&s_fx[k], fx);
+        atomicAdd(&s_fy[k], fy);
+        if (COUNT) atomicAdd(&s_cnt[k], cnt);
+    }
+}
+
+// Variant 2: pair queue.  Each lane walks the candidates of one owned bead at
+// a time (taking the next bead from a block-wide counter when it runs out, so
+// warps stay balanced); every candidate inside r_c is pushed, packed as
+// (i, j, Newton-3 flag, cell offset), into the warp's 128-entry buffer.
+// Whenever 32 pairs are queued the whole warp evaluates them together, so
+// the Philox and force arithmetic runs with every lane active.  Forces land
+// in shared memory through atomics on both sides of a Newton-3 pair.
+template <bool COUNT>
+__device__ __forceinline__ void queue_eval(const Sys &d, uint32_t code, const float2 *s_pos, const float2 *s_vel,
+                                           const uint32_t *s_id, float *s_fx, float *s_fy, uint32_t *s_cnt,
+                                           uint32_t s_lo, uint32_t s_hi)
+{
+    const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
+    const bool newton = (code >> 24) & 1u;
+    const int dcx = (int)((code >> 25) & 3u) - 1, dcy = (int)((code >> 27) & 3u) - 1;
+    const float2 oi = s_pos[k], pj = s_pos[j], vi = s_vel[k], vj = s_vel[j];
+    const float dx = shift_off(oi.x, dcx, d.cs) - pj.x, dy = shift_off(oi.y, dcy, d.cs) - pj.y;
+    const float r2 = dx * dx + dy * dy;
+    float ex, ey;
+    const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, s_id[k], s_id[j], s_lo, s_hi, r2, ex, ey);
+    const float gx = F * ex, gy = F * ey;
+    atomicAdd(&s_fx[k], gx);
+    atomicAdd(&s_fy[k], gy);
+    if (COUNT) atomicAdd(&s_cnt[k], 1u);
+    if (newton) {
+        atomicAdd(&s_fx[j], -gx);
+        atomicAdd(&s_fy[j], -gy);
+        if (COUNT) atomicAdd(&s_cnt[j], 1u);
+    }
+}
+
+template <int B, bool COUNT>
+__device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int th_, const int *s_cbeg,
+                                            const int *s_ccnt, const float2 *s_pos, const float2 *s_vel,
+                                            const uint32_t *s_id, float *s_fx, float *s_fy, uint32_t *s_cnt,
+                                            const unsigned char *s_lc, volatile uint32_t *q, int *s_next,
+                                            uint32_t s_lo, uint32_t s_hi)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int k = -1, j = 0, je = 0, lc0 = 0;
+    uint32_t visit = 0, own = 0, pid = 0, tag = 0;
+    float2 oi = make_float2(0.f, 0.f);
+    float pix = 0.f, piy = 0.f;
+    bool more = true;
+    int qn = 0;   // warp-uniform queue length (entries q[0, qn))
+    while (true) {
+        // At most one advance per lane per round (to the next neighbour
+        // range of its bead, or to its next bead), so a lane switching cells
+        // costs the warp one short divergent step instead of a loop.
+        bool have = j < je;
+        if (!have && more) {
+            if (visit == 0u) {
+                k = atomicAdd(s_next, 1);
+                if (k >= n_own) {
+                    more = false;
+                } else {
+                    oi = s_pos[k];
+                    const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
+                    lc0 = (ly + 1) * (B + 2) + lx + 1;
+                    pid = d.excl ? (s_id[k] ^ 1u) : 0xffffffffu;
+                    // which neighbour cells are owned by this tile (Newton-3 side)
+                    const uint32_t px = lx < tw - 1, nx = lx > 0, py = ly < th_ - 1, ny = ly > 0;
+                    own = 1u | (px << 1) | ((px & py) << 2) | (py << 3) | ((nx & py) << 4) | (nx << 5) |
+                          ((nx & ny) << 6) | (ny << 7) | ((px & ny) << 8);
+                    visit = 0x1fu | (~own & 0x1e0u);   // cells behind only when they are halo
+                }
+            }
+            if (more) {
+                const int nb = __ffs(visit) - 1;
+                visit &= visit - 1u;
+                const int ox_ = (int)((NB_DX >> (2 * nb)) & 3u) - 1, oy_ = (int)((NB_DY >> (2 * nb)) & 3u) - 1;
+                const int lc = lc0 + oy_ * (B + 2) + ox_;
+                j = s_cbeg[lc];
+                je = j + s_ccnt[lc];
+                if (nb == 0) j = k + 1;
+                pix = shift_off(oi.x, ox_, d.cs);
+                piy = shift_off(oi.y, oy_, d.cs);
+                tag = (uint32_t)k | (((own >> nb) & 1u) << 24) | ((uint32_t)(ox_ + 1) << 25) |
+                      ((uint32_t)(oy_ + 1) << 27);
+                have = j < je;
+            }
+        }
+        if (!__any_sync(FULL, have || more)) break;
+        // two candidates per lane per round (j and j + 1 while in range),
+        // tested branch-free; one append point per round
+        bool p0 = false, p1 = false;
+        uint32_t c0 = 0, c1 = 0;
+        if (have) {
+            const float2 pj = s_pos[j];
+            const float dx = pix - pj.x, dy = piy - pj.y;
+            const float r2 = dx * dx + dy * dy;
+            p0 = (r2 < d.rc2) & (r2 > 0.f) & (s_id[j] != pid);
+            c0 = tag | ((uint32_t)j << 12);
+            ++j;
+            if (j < je) {
+                const float2 pk = s_pos[j];
+                const float ex = pix - pk.x, ey = piy - pk.y;
+                const float s2 = ex * ex + ey * ey;
+                p1 = (s2 < d.rc2) & (s2 > 0.f) & (s_id[j] != pid);
+                c1 = tag | ((uint32_t)j << 12);
+                ++j;
+            }
+        }
+        const unsigned m0 = __ballot_sync(FULL, p0);
+        const unsigned m1 = __ballot_sync(FULL, p1);
+        const int n0 = __popc(m0);
+        if (p0) q[qn + __popc(m0 & lt)] = c0;
+        if (p1) q[qn + n0 + __popc(m1 & lt)] = c1;
+        qn += n0 + __popc(m1);
+        __syncwarp();
+        while (qn >= 32) {
+            // evaluate the oldest 32 entries, move the rest to the front
+            const uint32_t mine = q[lane];
+            const uint32_t carry0 = q[32 + lane], carry1 = q[64 + lane];
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = carry0;
+            if (lane + 32 < qn - 32) q[lane + 32] = carry1;
+            qn -= 32;
+            __syncwarp();
+            queue_eval<COUNT>(d, mine, s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lo, s_hi);
+        }
+    }
+    __syncwarp();
+    if (lane < qn) queue_eval<COUNT>(d, q[lane], s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lo, s_hi);
+}
+
 // Fused force + integrate for one tile.  Thread-per-owned-bead pair search:
 // pairs inside the tile are taken once (Newton-3 through shared-memory
 // atomics on the partner's slot), pairs with halo beads are taken from the
@@ -233,7 +437,7 @@ __device__ __forceinline__ float dpd_pair_scalar(const Sys &d, float dx, float d
 // random number), so every bead's force is complete when the tile finishes
 // and the integration runs in the same kernel.  A tile whose beads do not
 // fit in shared memory takes the same arithmetic from global memory.
-template <int B, bool COUNT>
+template <int B, bool COUNT, int VAR>
 __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *smem, Thermo3 &th)
 {
     using TP = TilePlan<B>;
@@ -254,8 +458,8 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     uint32_t *s_id = (uint32_t *)(s_vel + cap);
     float *s_fx = (float *)(s_id + cap);
     float *s_fy = s_fx + cap;
-    uint32_t *s_cnt = (uint32_t *)(s_fy + cap);
-    unsigned char *s_lc = (unsigned char *)(s_cnt + cap);
+    unsigned char *s_lc = (unsigned char *)(s_fy + cap);
+    uint32_t *s_cnt = (uint32_t *)(smem + ((TP::bead_off(NT) + (size_t)cap * 29 + 3) & ~size_t(3)));  // COUNT only
 
     const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
     const int x0 = tx * B, y0 = ty * B;
@@ -325,6 +529,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         }
         s_hbeg[nh] = run;
         s_sc[0] = run;
+        s_sc[1] = 0;   // next owned bead for the pair queue
     }
     __syncthreads();
     const int total = s_sc[0];
@@ -367,62 +572,13 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         __syncthreads();
 
         // ---- pair forces
-        for (int k = tid; k < n_own; k += NT) {
-            const float2 oi = s_pos[k], vi = s_vel[k];
-            const uint32_t idi = s_id[k], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
-            const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
-            float fx = 0.f, fy = 0.f;
-            uint32_t cnt = 0;
-#pragma unroll 1
-            for (int nb = 0; nb < 9; ++nb) {
-                int ox_ = 0, oy_ = 0;
-                switch (nb) {
-                    case 1: ox_ = 1; oy_ = 0; break;
-                    case 2: ox_ = 1; oy_ = 1; break;
-                    case 3: ox_ = 0; oy_ = 1; break;
-                    case 4: ox_ = -1; oy_ = 1; break;
-                    case 5: ox_ = -1; oy_ = 0; break;
-                    case 6: ox_ = -1; oy_ = -1; break;
-                    case 7: ox_ = 0; oy_ = -1; break;
-                    case 8: ox_ = 1; oy_ = -1; break;
-                    default: break;
-                }
-                const int nlx = lx + ox_, nly = ly + oy_;
-                // neighbours 1-4 lie ahead (E, NE, N, NW), 5-8 behind (W, SW, S, SE)
-                const bool owned = (nlx >= 0 && nlx < tw && nly >= 0 && nly < th_);
-                if (nb >= 5 && owned) continue;    // the other bead's forward sweep takes it
-                const bool newton = owned;
-                const float pix = oi.x - (float)ox_ * d.cs, piy = oi.y - (float)oy_ * d.cs;
-                const int lc = (nly + 1) * (B + 2) + nlx + 1;
-                int j = s_cbeg[lc];
-                const int je = j + s_ccnt[lc];
-                if (nb == 0) j = k + 1;
-                for (; j < je; ++j) {
-                    const float2 pj = s_pos[j];
-                    const float dx = pix - pj.x, dy = piy - pj.y;
-                    const float r2 = dx * dx + dy * dy;
-                    if (r2 < d.rc2 && r2 > 0.f) {
-                        const uint32_t idj = s_id[j];
-                        if (idj == pid) continue;
-                        const float2 vj = s_vel[j];
-                        float ex, ey;
-                        const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, idi, idj, s_lo,
-                                                        s_hi, r2, ex, ey);
-                        fx += F * ex;
-                        fy += F * ey;
-                        if (COUNT) ++cnt;
-                        if (newton) {
-                            atomicAdd(&s_fx[j], -F * ex);
-                            atomicAdd(&s_fy[j], -F * ey);
-                            if (COUNT) atomicAdd(&s_cnt[j], 1u);
-                        }
-                    }
-                }
-            }
-            atomicAdd(&s_fx[k], fx);
-            atomicAdd(&s_fy[k], fy);
-            if (COUNT) atomicAdd(&s_cnt[k], cnt);
-        }
+        if (VAR == 1)
+            pairs_thread<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lc,
+                                   s_lo, s_hi);
+        else
+            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lc,
+                                  (uint32_t *)(smem + TP::queue_off(cap, NT, COUNT)) + 128 * (tid >> 5), s_sc + 1, s_lo,
+                                  s_hi);
         __syncthreads();
 
         // ---- integrate owned beads

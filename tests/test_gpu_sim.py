@@ -69,11 +69,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("L,nd,tile,seed", CASES)
-def test_setup_force_parity(Sim, orc, L, nd, tile, seed):
+def test_setup_force_parity(Sim, orc, L, nd, tile, seed, variant):
     x, _ = synth.dimers(nd, L, 0.5, seed=seed)
     v = synth.velocities(2 * nd, 1.0, seed=seed + 10)
-    with Sim(L, 2 * nd, **sim_kw(seed=seed + 100, tile=tile)) as s:
+    with Sim(L, 2 * nd, **sim_kw(seed=seed + 100, tile=tile, variant=variant)) as s:
         s.set_positions(x, v, step=7)
         xg, vg, f, step = s.get_state()
         assert step == 7
@@ -95,10 +96,11 @@ def test_gaussian_noise_and_no_exclusion(Sim, orc):
     force_check(f, fo)
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("L,nd,tile,seed", CASES[:4])
-def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed):
+def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed, variant):
     x, _ = synth.dimers(nd, L, 0.5, seed=seed)
-    with Sim(L, 2 * nd, **sim_kw(tile=tile)) as s:
+    with Sim(L, 2 * nd, **sim_kw(tile=tile, variant=variant)) as s:
         s.set_positions(x)
         nc = s.info().n_cells_side
         assert nc == math.floor(L / 1.0)
