@@ -49,21 +49,24 @@ def filter_width(L, n_agents, n_f=10.0):
     return L * np.sqrt(n_f / n_agents)
 
 
-def velocity_field(c, vc, L, M, eps):
+def velocity_field(c, vc, L, M, eps, chunk=65536):
     """u_M on the M x M grid, layout [iy, ix, component]."""
     c = np.asarray(c, np.float64)
     vc = np.asarray(vc, np.float64)
     dx_grid = L / M
     xm = (np.arange(M) + 0.5) * dx_grid
     half = 0.5 * eps
-    # inclusion per axis, [agent, grid index]
-    ix = np.abs(_minimg(xm[None, :] - c[:, 0:1], L)) <= half
-    iy = np.abs(_minimg(xm[None, :] - c[:, 1:2], L)) <= half
-    ixf = ix.astype(np.float64)
-    iyf = iy.astype(np.float64)
-    n = iyf.T @ ixf                                   # [iy, ix]
-    sx = (iyf * vc[:, 0:1]).T @ ixf
-    sy = (iyf * vc[:, 1:2]).T @ ixf
+    n = np.zeros((M, M))
+    sx = np.zeros((M, M))
+    sy = np.zeros((M, M))
+    for a0 in range(0, c.shape[0], chunk):
+        cc, vv = c[a0:a0 + chunk], vc[a0:a0 + chunk]
+        # inclusion per axis, [agent, grid index]
+        ixf = (np.abs(_minimg(xm[None, :] - cc[:, 0:1], L)) <= half).astype(np.float64)
+        iyf = (np.abs(_minimg(xm[None, :] - cc[:, 1:2], L)) <= half).astype(np.float64)
+        n += iyf.T @ ixf                                  # [iy, ix]
+        sx += (iyf * vv[:, 0:1]).T @ ixf
+        sy += (iyf * vv[:, 1:2]).T @ ixf
     u = np.zeros((M, M, 2), np.float64)
     nz = n > 0
     u[..., 0][nz] = sx[nz] / n[nz]

@@ -1,0 +1,89 @@
+"""GPU parity of the Sec. 5.3-5.4 observables against the FP64 oracle.
+
+The device takes window and bin decisions with the same IEEE double
+operations as the oracle's definitions on the same (exact) positions, so
+window counts and pair counts must agree exactly; sums agree to rounding
+order (relative 1e-10 here).
+"""
+import numpy as np
+import pytest
+
+from oracle import observables as ob
+from paper_1310_0998_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1310_0998_gb300 import Sim
+    return Sim
+
+
+def _state(L, nd, seed, rc=1.0, r0=0.5):
+    x, _ = synth.dimers(nd, L, r0, seed=seed)
+    v = synth.velocities(2 * nd, 1.0, seed=seed + 3)
+    return x, v
+
+
+@pytest.mark.parametrize("L,nd,M,rc,r0", [(32.0, 512, 128, 1.0, 0.5), (37.0, 700, 64, 1.0, 0.5),
+                                          (100.0, 32000, 128, 0.5, 0.75)])
+def test_velocity_field_and_spectrum(Sim, L, nd, M, rc, r0):
+    x, v = _state(L, nd, 1, rc, r0)
+    with Sim(L, 2 * nd, rc=rc, r0=r0) as s:
+        s.set_positions(x, v)
+        u, n = s.velocity_field(M)
+        E = s.energy_spectrum(M)
+    c, vc = ob.agent_com(x, v, L)
+    eps = ob.filter_width(L, nd, 10.0)
+    uo, no = ob.velocity_field(c, vc, L, M, eps)
+    np.testing.assert_array_equal(n, no)
+    np.testing.assert_allclose(u, uo, rtol=1e-10, atol=1e-12)
+    Eo = ob.energy_spectrum(uo)
+    np.testing.assert_allclose(E, Eo, rtol=1e-9, atol=1e-15 * Eo.max())
+
+
+def test_explicit_filter_width_and_uniform_field(Sim):
+    L, nd, M = 64.0, 2000, 64
+    x, _ = synth.dimers(nd, L, 0.5, seed=2)
+    v = np.tile(np.array([[0.7, -0.2]], np.float32), (2 * nd, 1))
+    with Sim(L, 2 * nd) as s:
+        s.set_positions(x, v)
+        u, n = s.velocity_field(M, eps=4.0)
+        E = s.energy_spectrum(M, eps=4.0)
+    assert np.all(n > 0)
+    np.testing.assert_allclose(u[..., 0], 0.7, atol=1e-6)
+    np.testing.assert_allclose(u[..., 1], -0.2, atol=1e-6)
+    assert np.abs(E).max() < 1e-20
+
+
+@pytest.mark.parametrize("L,nd,dr,nbins", [(32.0, 512, 0.25, 64), (50.0, 4000, 0.5, 50)])
+def test_velocity_correlation(Sim, L, nd, dr, nbins):
+    x, v = _state(L, nd, 4)
+    with Sim(L, 2 * nd) as s:
+        s.set_positions(x, v)
+        g, Li, num, cnt = s.velocity_correlation(dr, nbins)
+    c, vc = ob.agent_com(x, v, L)
+    go, Lo, numo, cnto = ob.velocity_correlation(c, vc, L, dr, nbins)
+    np.testing.assert_array_equal(cnt, cnto)
+    np.testing.assert_allclose(num, numo, rtol=1e-10, atol=1e-9)
+    np.testing.assert_allclose(g, go, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(Li, Lo, rtol=1e-8, atol=1e-10)
+
+
+def test_spectrum_full_size(Sim):
+    """C3 geometry (1,572,864 agents): the field and E(k) on 128^2."""
+    L, nd, M = 1024.0, 3 * 1024 * 1024 // 2, 128
+    x, v = _state(L, nd, 0)
+    with Sim(L, 2 * nd) as s:
+        s.set_positions(x, v)
+        u, n = s.velocity_field(M)
+        E = s.energy_spectrum(M)
+    c, vc = ob.agent_com(x, v, L)
+    eps = ob.filter_width(L, nd, 10.0)
+    uo, no = ob.velocity_field(c, vc, L, M, eps)
+    np.testing.assert_array_equal(n, no)
+    np.testing.assert_allclose(u, uo, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(E, ob.energy_spectrum(uo), rtol=1e-9)
