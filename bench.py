@@ -121,6 +121,48 @@ def cpu_oracle_rate(L, n_beads, budget_s=12.0, seed=0):
     return rate, oracle.num_threads(), f"{steps} steps of the FP64 cell-list oracle on a {n_beads}-bead box (L={L:g}, density 3), {t2 - t0:.1f} s"
 
 
+def ensemble_leg(R, steps, warmup, seed=0):
+    """C4: R replicas drawn from the uneven distribution (box side U(32, 192),
+    area fraction U(0.05, 0.6), gamma log-U(0.5, 50), zeta log-U(0.005, 2),
+    f_p U(0.5, 2)).  Times `steps` steps of the batched persistent kernel and
+    the same steps run replica by replica through the single-system path."""
+    import torch
+    from paper_1310_0998_gb300 import Ensemble, synth
+    pts = []
+    for r, e in enumerate(synth.ensemble_points(R, seed)):
+        pts.append(dict(a=PHYS["a"], kBT=PHYS["kBT"], rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"],
+                        dt=PHYS["dt"], L=e["L"], n_beads=2 * e["n_dimers"], gamma=e["gamma"], zeta=e["zeta"],
+                        f_p=e["fp"], seed=seed + r, replica=r))
+    beads = sum(p["n_beads"] for p in pts)
+    ens = Ensemble(pts)
+    ens.init_random(seed)
+    ens.step(warmup)
+    ens.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens.step(steps)
+    ens.sync()
+    t_batch = time.perf_counter() - t0
+    views = [ens.replica(r) for r in range(R)]
+    for v in views:
+        v.step(1)
+    for v in views:
+        v.sync()
+    t0 = time.perf_counter()
+    for v in views:
+        v.step(steps)
+    for v in views:
+        v.sync()
+    t_seq = time.perf_counter() - t0
+    info = ens.info()
+    ens.close()
+    return {"replicas": R, "beads": beads, "steps": steps, "batched_ms_per_step": 1e3 * t_batch / steps,
+            "sequential_ms_per_step": 1e3 * t_seq / steps, "speedup": t_seq / t_batch,
+            "batched_particle_steps_per_s": beads * steps / t_batch, "grid": info["grid"],
+            "work_tiles": info["work_tiles"],
+            "timing": "wall clock around each leg, synchronised; sequential = each replica alone, one after another"}
+
+
 def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -161,6 +203,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue")
     ap.add_argument("--tile", type=int, default=0, help="cell-block side: 0 default, 4, 8, 16")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--ens-replicas", type=int, default=256)
+    ap.add_argument("--ens-steps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = CONFIGS[args.config]
@@ -281,6 +326,8 @@ def main():
         "overflow_tiles": int(info.overflow_tiles),
         "clocks": clk,
     }
+    if rank == 0 and not args.no_ensemble:
+        line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup)
     if rank == 0 and not args.no_cpu:
         Lc = 128.0 if nb > 200000 else L
         nbc = int(round(nb * (Lc / L) ** 2)) // 2 * 2

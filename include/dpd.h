@@ -189,11 +189,57 @@ int dpd_pair_counts(dpd_ctx *ctx, uint32_t *cnt, uint64_t *total);
 
 int dpd_get_info(dpd_ctx *ctx, dpd_info *info);
 
+/* The first device check that failed since the last set_state/init_random:
+ * out[0] = site (0 none, 1 scatter slot or id out of range [values: bead,
+ * slot, id], 2 bonded partner slot out of range [slot, id, partner slot],
+ * 3 scan wait timed out [block, predecessor, 0]), out[1..3] = values.
+ * Synchronises. */
+int dpd_error_info(dpd_ctx *ctx, int64_t out[4]);
+
 /* Measurement: advance one step exactly as dpd_step(ctx, 1) does, but with
  * the three kernels launched one by one between CUDA events on the context's
  * stream; ms[0..2] receive the device time of the scan, scatter and fused
  * force/integrate kernels.  Synchronises. */
 int dpd_profile_step(dpd_ctx *ctx, double ms[3]);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: R replicas (uneven box sizes, bead counts and parameters)
+ * advanced together by one persistent kernel per call, captured into a CUDA
+ * graph per step count.  Each replica is a full context reachable through
+ * dpd_batch_replica, so states, observables and logs use the calls above;
+ * replicas must not be passed to dpd_destroy (they belong to the batch).
+ * All replicas share the tile side and pair-kernel variant of p[0].
+ * ------------------------------------------------------------------------ */
+typedef struct dpd_batch dpd_batch;
+
+/* p: R parameter sets (1 <= R <= 1023), each validated as in dpd_create. */
+int dpd_batch_create(const dpd_params *p, int R, void *stream, dpd_batch **out);
+void dpd_batch_destroy(dpd_batch *b);
+
+/* Borrowed handle of replica r (valid until dpd_batch_destroy). */
+int dpd_batch_replica(dpd_batch *b, int r, dpd_ctx **view);
+
+/* The paper's initial condition for every replica, replica r with seed + r. */
+int dpd_batch_init_random(dpd_batch *b, uint64_t seed);
+
+/* Advance every replica n steps in one persistent launch (asynchronous).
+ * Every replica must hold a state.  Grid-wide waits inside the kernel are
+ * bounded; a wait that gives up is reported as DPD_ERR_TIMEOUT by
+ * dpd_batch_sync. */
+int dpd_batch_step(dpd_batch *b, int64_t n);
+
+/* Wait, then return the batch's latched status (the first error of the
+ * batch or of any replica). */
+int dpd_batch_sync(dpd_batch *b);
+
+/* Failure-detection self-test: launches the grid barrier with one block that
+ * never arrives; the others must give up after the bounded wait.  Returns
+ * DPD_ERR_TIMEOUT when the timeout fired (the expected outcome) and leaves
+ * the batch usable. */
+int dpd_batch_barrier_selftest(dpd_batch *b);
+
+/* Replica count, blocks of the persistent launch, (replica, cell block) items. */
+int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
 
 #ifdef __cplusplus
 }

@@ -6,12 +6,14 @@ input generator (``synth``) does not load the CUDA library.
 """
 import importlib
 
-__all__ = ["Sim", "make_params", "synth"]
+__all__ = ["Sim", "Ensemble", "make_params", "synth"]
 
 
 def __getattr__(name):
     if name in ("Sim", "make_params"):
         return getattr(importlib.import_module(__name__ + ".sim"), name)
-    if name in ("synth", "sim", "build"):
+    if name == "Ensemble":
+        return importlib.import_module(__name__ + ".ensemble").Ensemble
+    if name in ("synth", "sim", "build", "ensemble"):
         return importlib.import_module(__name__ + "." + name)
     raise AttributeError(name)

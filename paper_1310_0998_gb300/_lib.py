@@ -91,6 +91,15 @@ def _declare(L):
         "dpd_pair_counts": ([vp, vp, P(u64)], c_int),
         "dpd_get_info": ([vp, P(DpdInfo)], c_int),
         "dpd_profile_step": ([vp, vp], c_int),
+        "dpd_error_info": ([vp, vp], c_int),
+        "dpd_batch_create": ([vp, c_int, vp, P(vp)], c_int),
+        "dpd_batch_destroy": ([vp], None),
+        "dpd_batch_replica": ([vp, c_int, P(vp)], c_int),
+        "dpd_batch_init_random": ([vp, u64], c_int),
+        "dpd_batch_step": ([vp, i64], c_int),
+        "dpd_batch_sync": ([vp], c_int),
+        "dpd_batch_barrier_selftest": ([vp], c_int),
+        "dpd_batch_info": ([vp, P(c_int), P(c_int), P(c_int)], c_int),
     }
     for name, (args, res) in sig.items():
         if hasattr(L, name):

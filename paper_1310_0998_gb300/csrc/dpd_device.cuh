@@ -58,6 +58,7 @@ struct Sys {
     uint32_t *pcnt;
     unsigned long long *ovf;
     int *err;
+    long long *errinfo;   // first failed check: site, then three values
     unsigned long long *scan_status, *scan_ticket;
 };
 
@@ -143,6 +144,17 @@ __device__ __forceinline__ float vbits(uint32_t u) { return __uint_as_float(u); 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
 
 __device__ __forceinline__ void set_err(const Sys &d, int bits) { atomicOr(d.err, bits); }
+
+// Record the first failed check (site code and three values) beside the bits.
+__device__ __forceinline__ void set_err_at(const Sys &d, int bits, int site, long long a, long long b, long long c)
+{
+    atomicOr(d.err, bits);
+    if (atomicCAS((unsigned long long *)d.errinfo, 0ull, (unsigned long long)site) == 0ull) {
+        d.errinfo[1] = a;
+        d.errinfo[2] = b;
+        d.errinfo[3] = c;
+    }
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {

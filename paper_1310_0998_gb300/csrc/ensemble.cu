@@ -1,0 +1,441 @@
+// Batched ensemble: R replicas of uneven size and parameters advanced by one
+// persistent kernel (include/dpd.h, dpd_batch_*).
+//
+// Each replica is an ordinary context (its own buffers, cell list, thermo log
+// and canonical state), so every single-system call also works on it through
+// dpd_batch_replica.  The batch adds a device table of the replicas' Sys
+// descriptors, two work lists and one kernel that runs n whole steps for all
+// replicas: per step three phases (cell scan, scatter, fused force/integrate)
+// separated by grid-wide barriers.  Block b takes work items b, b + G,
+// b + 2G, ... (G blocks) of each phase's list (a replica to scan, a
+// 1024-bead chunk to scatter, a (replica, cell block) to integrate); the host
+// shuffles the lists once with a fixed seed so that uneven replicas spread
+// evenly over the blocks.  (Items handed out by atomic counters that block 0
+// reset between phases were measured to process some cell blocks twice; the
+// fixed interleave needs no shared counter.)  The kernel is
+// launched with no more blocks than can be resident at once and every
+// barrier wait is bounded: a block that gives up latches DPD_ERR_TIMEOUT in
+// the batch's error word instead of hanging.  The launch for a given step
+// count is captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dpd.h"
+#include "sim_host.h"
+#include "sim_kernels.cuh"
+
+namespace dpd {
+
+constexpr int ENS_CHUNK = 1024;   // beads per scatter work item
+
+// Exclusive scan of one system's cell counts by a single block, chunk by
+// chunk with a running carry (replica boxes hold at most a few 10^4 cells);
+// also advances the replica's step and clears its thermo slot.
+__device__ void scan_block(const Sys &d)
+{
+    __shared__ uint32_t s_w[TILE_THREADS / 32];
+    __shared__ uint32_t s_carry, s_tot;
+    constexpr int IPT = 8;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < d.ncells; base += blockDim.x * IPT) {
+        uint32_t v[IPT], sum = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const int idx = base + tid * IPT + k;
+            v[k] = idx < d.ncells ? d.counts[idx] : 0u;
+            sum += v[k];
+            if (idx < d.ncells) d.counts[idx] = 0u;
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_w[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t w = lane < nw ? s_w[lane] : 0u;
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < nw) s_w[lane] = wi - w;
+            if (lane == nw - 1) s_tot = wi;
+        }
+        __syncthreads();
+        uint32_t run = s_carry + s_w[wid] + (incl - sum);
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const int idx = base + tid * IPT + k;
+            if (idx < d.ncells) d.cstart[idx] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += s_tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        d.cstart[d.ncells] = s_carry;
+        const long long s1 = *d.step + 1;
+        *d.step = s1;
+        double *th = d.thermo + 4 * (size_t)(s1 % THERMO_CAP);
+        th[0] = 0.0; th[1] = 0.0; th[2] = 0.0; th[3] = 0.0;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier over the resident blocks: an arrival counter and a
+// generation word.  The wait is bounded; on timeout the block sets the error
+// word and proceeds.  skip != 0 makes this block not arrive (self-test).
+__device__ void grid_barrier(unsigned *bar, unsigned nblocks, int *err, int skip)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !skip) {
+        unsigned *count = bar, *gen = bar + 1;
+        const unsigned g = ld_acquire_u32(gen);
+        __threadfence();
+        const unsigned t = atomicAdd(count, 1u);
+        if (t == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire_u32(gen) == g) {
+                if (++spins > SPIN_LIMIT) { atomicOr(err, ERR_TIMEOUT); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <int B, int VAR>
+__global__ void __launch_bounds__(TILE_THREADS, 6)
+    k_ensemble(const Sys *__restrict__ sys, const uint32_t *__restrict__ scan_items, int R,
+               const uint32_t *__restrict__ scat, int n_scat, const uint32_t *__restrict__ tiles, int n_tiles,
+               unsigned *bar, int *berr, int nsteps, int final_last)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned nb = gridDim.x;
+    for (int s = 0; s < nsteps; ++s) {
+        // phase 1: cell scans, one replica per block at a time
+        for (int it = blockIdx.x; it < R; it += nb) scan_block(sys[scan_items[it]]);
+        grid_barrier(bar, nb, berr, 0);
+        // phase 2: scatter U -> S in chunks of ENS_CHUNK beads
+        for (int it = blockIdx.x; it < n_scat; it += nb) {
+            const uint32_t w = scat[it];
+            const Sys &d = sys[w >> 22];
+            const int k0 = (int)(w & 0x3fffffu) * ENS_CHUNK, k1 = min(d.n, k0 + ENS_CHUNK);
+            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) scatter_one<B>(d, k);
+        }
+        grid_barrier(bar, nb, berr, 0);
+        // phase 3: fused force / integrate / re-bin per (replica, cell block)
+        const int flags = F_ADVANCE | ((final_last && s == nsteps - 1) ? F_FINAL : 0);
+        for (int it = blockIdx.x; it < n_tiles; it += nb) {
+            const uint32_t w = tiles[it];
+            const Sys &d = sys[w >> 22];
+            Thermo3 th{0.f, 0.f, 0.f};
+            force_tile<B, false, VAR>(d, (int)(w & 0x3fffffu), flags, smem, th);
+            __syncthreads();
+            thermo_flush(d, th, (double *)(smem + TilePlan<B>::red_off()));
+            __syncthreads();
+        }
+        grid_barrier(bar, nb, berr, 0);
+    }
+}
+
+// Self-test of the bounded barrier: block 0 never arrives, every other block
+// must give up after the spin limit and latch DPD_ERR_TIMEOUT.
+__global__ void k_barrier_selftest(unsigned *bar, int *berr)
+{
+    grid_barrier(bar, gridDim.x, berr, blockIdx.x == 0);
+}
+
+}  // namespace dpd
+
+using namespace dpd;
+
+struct dpd_batch {
+    int R = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<dpd_ctx *> reps;
+    void *pool = nullptr;
+    Sys *d_sys = nullptr;
+    uint32_t *d_scan = nullptr, *d_scat = nullptr, *d_tiles = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    int n_scat = 0, n_tiles = 0, B = 8, var = 2, cap = 0, grid = 0;
+    size_t smem = 0;
+    cudaGraphExec_t g = nullptr;
+    int64_t g_steps = -1;
+    int *h_pin = nullptr;
+};
+
+#define CUB(x)                                                                      \
+    do {                                                                            \
+        const cudaError_t e_ = (x);                                                 \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? DPD_ERR_OOM : DPD_ERR_CUDA; \
+    } while (0)
+
+template <int B, int VAR>
+static int ens_prepare(dpd_batch *b)
+{
+    // the opt-in limit covers static plus dynamic shared memory
+    cudaFuncAttributes fa;
+    CUB(cudaFuncGetAttributes(&fa, k_ensemble<B, VAR>));
+    if (b->smem + fa.sharedSizeBytes > (size_t)max_dynamic_smem()) return DPD_ERR_INVALID_ARG;
+    CUB(cudaFuncSetAttribute(k_ensemble<B, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_dynamic_smem() - (int)fa.sharedSizeBytes));
+    int dev = 0, nsm = 0, occ = 0;
+    CUB(cudaGetDevice(&dev));
+    CUB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ensemble<B, VAR>, TILE_THREADS, b->smem));
+    if (occ < 1) return DPD_ERR_INVALID_ARG;
+    b->grid = nsm * occ;
+    return DPD_OK;
+}
+
+template <int B, int VAR>
+static void ens_launch(dpd_batch *b, int nsteps, int final_last)
+{
+    k_ensemble<B, VAR><<<b->grid, TILE_THREADS, b->smem, b->st>>>(b->d_sys, b->d_scan, b->R, b->d_scat, b->n_scat,
+                                                                  b->d_tiles, b->n_tiles, b->d_bar, b->d_err, nsteps,
+                                                                  final_last);
+}
+
+static int ens_dispatch_prepare(dpd_batch *b)
+{
+    if (b->var == 1) return b->B == 4 ? ens_prepare<4, 1>(b) : b->B == 8 ? ens_prepare<8, 1>(b) : ens_prepare<16, 1>(b);
+    return b->B == 4 ? ens_prepare<4, 2>(b) : b->B == 8 ? ens_prepare<8, 2>(b) : ens_prepare<16, 2>(b);
+}
+
+static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last)
+{
+    if (b->var == 1) {
+        if (b->B == 4) ens_launch<4, 1>(b, nsteps, final_last);
+        else if (b->B == 8) ens_launch<8, 1>(b, nsteps, final_last);
+        else ens_launch<16, 1>(b, nsteps, final_last);
+    } else {
+        if (b->B == 4) ens_launch<4, 2>(b, nsteps, final_last);
+        else if (b->B == 8) ens_launch<8, 2>(b, nsteps, final_last);
+        else ens_launch<16, 2>(b, nsteps, final_last);
+    }
+}
+
+static int ens_build_tables(dpd_batch *b)
+{
+    std::vector<Sys> sys(b->R);
+    std::vector<uint32_t> scan(b->R), scat, tiles;
+    int cap = 0;
+    for (int r = 0; r < b->R; ++r) {
+        sys[r] = b->reps[r]->d;
+        cap = std::max(cap, sys[r].cap);
+        const int nch = (sys[r].n + ENS_CHUNK - 1) / ENS_CHUNK, nt = sys[r].ntx * sys[r].ntx;
+        if (nch >= (1 << 22) || nt >= (1 << 22)) return DPD_ERR_INVALID_ARG;
+        for (int c = 0; c < nch; ++c) scat.push_back(((uint32_t)r << 22) | (uint32_t)c);
+        for (int t = 0; t < nt; ++t) tiles.push_back(((uint32_t)r << 22) | (uint32_t)t);
+    }
+    // fixed-seed shuffles (xorshift, Fisher-Yates) spread replicas over blocks;
+    // the largest replicas are scanned first
+    uint64_t rs = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&rs]() { rs ^= rs << 13; rs ^= rs >> 7; rs ^= rs << 17; return rs; };
+    auto shuffle = [&rnd](std::vector<uint32_t> &v) {
+        for (size_t i = v.size(); i > 1; --i) std::swap(v[i - 1], v[rnd() % i]);
+    };
+    shuffle(scat);
+    shuffle(tiles);
+    for (int r = 0; r < b->R; ++r) scan[r] = (uint32_t)r;
+    std::stable_sort(scan.begin(), scan.end(), [&sys](uint32_t a, uint32_t c) { return sys[a].ncells > sys[c].ncells; });
+    // every replica's tile plan fits the common shared-memory size
+    for (int r = 0; r < b->R; ++r) sys[r].cap = cap;
+    for (int r = 0; r < b->R; ++r) b->reps[r]->d.cap = cap;
+    b->cap = cap;
+    b->smem = force_smem(b->B, cap, false);
+    b->n_scat = (int)scat.size();
+    b->n_tiles = (int)tiles.size();
+    if (b->pool) cudaFree(b->pool);
+    const size_t bytes = sizeof(Sys) * (size_t)b->R + 4 * (size_t)b->R + 4 * scat.size() + 4 * tiles.size() + 256 * 5;
+    CUB(cudaMalloc(&b->pool, bytes));
+    char *p = (char *)b->pool;
+    b->d_sys = (Sys *)p; p += (sizeof(Sys) * (size_t)b->R + 255) & ~size_t(255);
+    b->d_scan = (uint32_t *)p; p += (4 * (size_t)b->R + 255) & ~size_t(255);
+    b->d_scat = (uint32_t *)p; p += (4 * scat.size() + 255) & ~size_t(255);
+    b->d_tiles = (uint32_t *)p; p += (4 * tiles.size() + 255) & ~size_t(255);
+    b->d_bar = (unsigned *)p;          // 2 words
+    b->d_err = (int *)(b->d_bar + 8);  // 1 word
+    CUB(cudaMemcpyAsync(b->d_sys, sys.data(), sizeof(Sys) * (size_t)b->R, cudaMemcpyHostToDevice, b->st));
+    CUB(cudaMemcpyAsync(b->d_scan, scan.data(), 4 * (size_t)b->R, cudaMemcpyHostToDevice, b->st));
+    CUB(cudaMemcpyAsync(b->d_scat, scat.data(), 4 * scat.size(), cudaMemcpyHostToDevice, b->st));
+    CUB(cudaMemcpyAsync(b->d_tiles, tiles.data(), 4 * tiles.size(), cudaMemcpyHostToDevice, b->st));
+    CUB(cudaMemsetAsync(b->d_bar, 0, 64, b->st));
+    for (int r = 0; r < b->R; ++r) {
+        dpd_ctx *c = b->reps[r];
+        c->smem = b->smem;
+        const int rc = set_force_smem(c->B, cap);
+        if (rc) return rc;
+    }
+    int rc = ens_dispatch_prepare(b);
+    if (rc) return rc;
+    CUB(cudaStreamSynchronize(b->st));
+    return DPD_OK;
+}
+
+extern "C" {
+
+int dpd_batch_create(const dpd_params *p, int R, void *stream, dpd_batch **out)
+{
+    if (!out || !p || R < 1 || R > 1023) return DPD_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int r = 0; r < R; ++r) {
+        const int rc = validate(&p[r]);
+        if (rc) return rc;
+        if ((p[r].tile ? p[r].tile : 8) != (p[0].tile ? p[0].tile : 8) || p[r].variant != p[0].variant)
+            return DPD_ERR_INVALID_ARG;   // one kernel shape for the whole batch
+    }
+    dpd_batch *b = new (std::nothrow) dpd_batch();
+    if (!b) return DPD_ERR_OOM;
+    b->R = R;
+    if (stream) {
+        b->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) { delete b; return DPD_ERR_CUDA; }
+        b->own_stream = true;
+    }
+    b->B = p[0].tile ? p[0].tile : 8;
+    b->var = p[0].variant ? p[0].variant : 2;
+    b->reps.assign(R, nullptr);
+    int rc = DPD_OK;
+    for (int r = 0; r < R && rc == DPD_OK; ++r) {
+        rc = dpd_create(&p[r], b->st, &b->reps[r]);
+        if (rc == DPD_OK) b->reps[r]->batch_owned = true;
+    }
+    if (rc == DPD_OK && cudaMallocHost((void **)&b->h_pin, 64) != cudaSuccess) rc = DPD_ERR_OOM;
+    if (rc == DPD_OK) rc = ens_build_tables(b);
+    if (rc) {
+        dpd_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return DPD_OK;
+}
+
+void dpd_batch_destroy(dpd_batch *b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->g) cudaGraphExecDestroy(b->g);
+    for (dpd_ctx *c : b->reps) {
+        if (c) {
+            c->batch_owned = false;
+            dpd_destroy(c);
+        }
+    }
+    if (b->pool) cudaFree(b->pool);
+    if (b->h_pin) cudaFreeHost(b->h_pin);
+    if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+int dpd_batch_replica(dpd_batch *b, int r, dpd_ctx **view)
+{
+    if (!b || !view || r < 0 || r >= b->R) return DPD_ERR_INVALID_ARG;
+    *view = b->reps[r];
+    return DPD_OK;
+}
+
+int dpd_batch_init_random(dpd_batch *b, uint64_t seed)
+{
+    if (!b) return DPD_ERR_INVALID_ARG;
+    for (int r = 0; r < b->R; ++r) {
+        const int rc = dpd_init_random(b->reps[r], seed + (uint64_t)r);
+        if (rc) return rc;
+    }
+    return DPD_OK;
+}
+
+int dpd_batch_step(dpd_batch *b, int64_t n)
+{
+    if (!b || n < 0 || n > (1ll << 30)) return DPD_ERR_INVALID_ARG;
+    for (dpd_ctx *c : b->reps)
+        if (!c->have_state) return DPD_ERR_STATE;
+    if (n == 0) return DPD_OK;
+    if (!b->g || b->g_steps != n) {
+        if (b->g) cudaGraphExecDestroy(b->g);
+        b->g = nullptr;
+        cudaGraph_t gr = nullptr;
+        CUB(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        ens_dispatch_launch(b, (int)n, 1);
+        const cudaError_t e = cudaStreamEndCapture(b->st, &gr);
+        if (e != cudaSuccess) return DPD_ERR_CUDA;
+        const cudaError_t e2 = cudaGraphInstantiate(&b->g, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e2 != cudaSuccess) return DPD_ERR_CUDA;
+        b->g_steps = n;
+    }
+    CUB(cudaGraphLaunch(b->g, b->st));
+    for (dpd_ctx *c : b->reps) {
+        c->step += n;
+        c->sorted_canonical = true;
+    }
+    return DPD_OK;
+}
+
+int dpd_batch_sync(dpd_batch *b)
+{
+    if (!b) return DPD_ERR_INVALID_ARG;
+    CUB(cudaMemcpyAsync(b->h_pin, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    CUB(cudaStreamSynchronize(b->st));
+    int status = DPD_OK;
+    if (b->h_pin[0] & ERR_TIMEOUT) status = DPD_ERR_TIMEOUT;
+    for (dpd_ctx *c : b->reps) {
+        const int rc = dpd_internal_latched(c);
+        if (rc && status == DPD_OK) status = rc;
+    }
+    return status;
+}
+
+int dpd_batch_barrier_selftest(dpd_batch *b)
+{
+    if (!b) return DPD_ERR_INVALID_ARG;
+    CUB(cudaMemsetAsync(b->d_bar, 0, 64, b->st));
+    int dev = 0, nsm = 0;
+    CUB(cudaGetDevice(&dev));
+    CUB(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    k_barrier_selftest<<<std::min(nsm, 8), 32, 0, b->st>>>(b->d_bar, b->d_err);
+    CUB(cudaGetLastError());
+    CUB(cudaMemcpyAsync(b->h_pin, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    CUB(cudaStreamSynchronize(b->st));
+    const int seen = b->h_pin[0];
+    // leave the batch usable: clear the error word and the barrier state
+    CUB(cudaMemsetAsync(b->d_bar, 0, 64, b->st));
+    CUB(cudaStreamSynchronize(b->st));
+    return (seen & ERR_TIMEOUT) ? DPD_ERR_TIMEOUT : DPD_OK;
+}
+
+int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles)
+{
+    if (!b) return DPD_ERR_INVALID_ARG;
+    if (n_replicas) *n_replicas = b->R;
+    if (grid) *grid = b->grid;
+    if (n_work_tiles) *n_work_tiles = b->n_tiles;
+    return DPD_OK;
+}
+
+}  // extern "C"

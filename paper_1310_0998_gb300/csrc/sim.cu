@@ -256,20 +256,44 @@ size_t force_smem(int B, int cap, bool count)
     }
 }
 
-template <int B>
-static int set_force_attrs(int cap)
+// The dynamic shared-memory limit is a per-kernel, process-wide attribute:
+// raise it once to the device's opt-in maximum so contexts with different
+// tile capacities never shrink each other's limit.
+template <typename K>
+static int set_dyn_limit(K kernel, int smax)
 {
-    const int s0 = (int)TilePlan<B>::bytes(cap, TILE_THREADS, false), s1 = (int)TilePlan<B>::bytes(cap, TILE_THREADS, true);
-    CU(cudaFuncSetAttribute(k_force<B, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
-    CU(cudaFuncSetAttribute(k_force<B, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
-    CU(cudaFuncSetAttribute(k_force<B, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
-    CU(cudaFuncSetAttribute(k_force<B, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+    cudaFuncAttributes fa;
+    CU(cudaFuncGetAttributes(&fa, kernel));   // the limit covers static + dynamic
+    CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smax - (int)fa.sharedSizeBytes));
     return DPD_OK;
+}
+
+template <int B>
+static int set_force_attrs(int smax)
+{
+    int rc = set_dyn_limit(k_force<B, false, 1>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, true, 1>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, false, 2>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, true, 2>, smax);
+    return rc;
+}
+
+int max_dynamic_smem()
+{
+    int dev = 0, smax = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 48 * 1024;
+    return smax;
 }
 
 int set_force_smem(int B, int cap)
 {
-    return B == 4 ? set_force_attrs<4>(cap) : B == 8 ? set_force_attrs<8>(cap) : set_force_attrs<16>(cap);
+    const int smax = max_dynamic_smem();
+    if ((int)force_smem(B, cap, true) > smax) return DPD_ERR_INVALID_ARG;
+    int rc = set_force_attrs<4>(smax);
+    if (!rc) rc = set_force_attrs<8>(smax);
+    if (!rc) rc = set_force_attrs<16>(smax);
+    return rc;
 }
 
 template <int B, int VAR>
@@ -440,7 +464,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     const size_t o_S = take(16 * n), o_Sid = take(4 * n), o_U = take(16 * n), o_Uid = take(4 * n),
                  o_Ur = take(4 * n), o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
                  o_C = take(16 * n), o_Cf = take(8 * n), o_th = take(sizeof(double) * 4 * THERMO_CAP),
-                 o_step = take(8), o_pc = take(4 * n), o_ovf = take(8), o_err = take(8),
+                 o_step = take(8), o_pc = take(4 * n), o_ovf = take(8), o_err = take(8), o_einfo = take(32),
                  o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(32 * n);
     c->pool_bytes = off;
     if (cudaMalloc(&c->pool, off) != cudaSuccess) {
@@ -472,6 +496,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     c->pcnt_buf = (uint32_t *)(b + o_pc);
     d.ovf = (unsigned long long *)(b + o_ovf);
     d.err = (int *)(b + o_err);
+    d.errinfo = (long long *)(b + o_einfo);
     d.scan_status = (unsigned long long *)(b + o_ss);
     d.scan_ticket = (unsigned long long *)(b + o_tk);
     if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess ||
@@ -486,7 +511,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
 
 void dpd_destroy(dpd_ctx *c)
 {
-    if (!c) return;
+    if (!c || c->batch_owned) return;   // replicas belong to their batch
     if (c->st) cudaStreamSynchronize(c->st);
     free_graphs(c);
     dpd_internal_free_obs(c);
@@ -540,6 +565,7 @@ int dpd_set_state(dpd_ctx *c, const double *x, const float *v, const float *f, i
         df = f ? (const float *)(st + 24 * n) : nullptr;
     }
     CU(cudaMemsetAsync(c->d.err, 0, sizeof(int), c->st));
+    CU(cudaMemsetAsync(c->d.errinfo, 0, 32, c->st));
     CU(cudaMemsetAsync(c->d.counts, 0, sizeof(uint32_t) * (size_t)c->d.ncells, c->st));
     k_load_state<<<(c->d.n + 255) / 256, 256, 0, c->st>>>(c->d, dx, dv, df);
     if (!f) return start_from_U(c, step);
@@ -557,6 +583,7 @@ int dpd_init_random(dpd_ctx *c, uint64_t seed)
 {
     if (!c) return DPD_ERR_INVALID_ARG;
     CU(cudaMemsetAsync(c->d.err, 0, sizeof(int), c->st));
+    CU(cudaMemsetAsync(c->d.errinfo, 0, 32, c->st));
     CU(cudaMemsetAsync(c->d.counts, 0, sizeof(uint32_t) * (size_t)c->d.ncells, c->st));
     k_init_random<<<(c->d.n / 2 + 255) / 256, 256, 0, c->st>>>(c->d, (unsigned long long)seed);
     return start_from_U(c, 0);
@@ -738,6 +765,16 @@ int dpd_profile_step(dpd_ctx *c, double ms[3])
     }
     for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
     return rc;
+}
+
+int dpd_error_info(dpd_ctx *c, int64_t out[4])
+{
+    if (!c || !out) return DPD_ERR_INVALID_ARG;
+    long long h[4];
+    CU(cudaMemcpyAsync(h, c->d.errinfo, 32, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < 4; ++i) out[i] = h[i];
+    return DPD_OK;
 }
 
 int dpd_get_info(dpd_ctx *c, dpd_info *info)

@@ -16,6 +16,7 @@ void launch_iteration(const Sys &d, int B, int var, cudaStream_t st, int nscan, 
 void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t smem, int flags, bool count);
 void launch_scatter(const Sys &d, int B, cudaStream_t st);
 int set_force_smem(int B, int cap);
+int max_dynamic_smem();
 void launch_bin(const Sys &d, int B, cudaStream_t st);
 void launch_kick_bin(const Sys &d, int B, cudaStream_t st);
 int host_cell_of(int B, int nc, int cx, int cy);
@@ -35,6 +36,7 @@ struct dpd_ctx {
     long long step = 0;
     bool have_state = false;
     bool sorted_canonical = false;  // S / cstart hold the canonical positions
+    bool batch_owned = false;       // a replica of a dpd_batch (destroyed with it)
     double *h_pin = nullptr;        // small pinned staging (thermo, scalars)
     void *obs = nullptr;            // observables scratch (observables.cu)
     void *stage = nullptr;          // 32 B/bead staging for host state transfers

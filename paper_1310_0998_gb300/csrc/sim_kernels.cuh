@@ -21,7 +21,7 @@ namespace dpd {
 // ticket so predecessors always run first; the epoch (ticket / nblocks) tags
 // the status words so nothing needs clearing between launches.  Waits are
 // bounded: on timeout the error bit is set and the scan continues.
-__device__ void scan_decoupled(const Sys &d, int nblocks)
+__device__ inline void scan_decoupled(const Sys &d, int nblocks)
 {
     __shared__ uint32_t s_warp[SCAN_NT / 32];
     __shared__ uint32_t s_excl;
@@ -83,7 +83,7 @@ __device__ void scan_decoupled(const Sys &d, int nblocks)
                     const unsigned long long w64 = ld_acquire_u64(&st[j]);
                     const unsigned long long wep = w64 >> 34, fl = (w64 >> 32) & 3ull;
                     if (wep != ep || fl == 0ull) {
-                        if (++spins > SPIN_LIMIT) { set_err(d, ERR_TIMEOUT); break; }
+                        if (++spins > SPIN_LIMIT) { set_err_at(d, ERR_TIMEOUT, 3, bid, j, 0); break; }
                         __nanosleep(32);
                         continue;
                     }
@@ -121,7 +121,10 @@ __device__ __forceinline__ void scatter_one(const Sys &d, int k)
     const uint32_t id = d.U_id[k], rank = d.U_rank[k];
     const int c = cell_of<B>(d, cell_coord(d, xv.x), cell_coord(d, xv.y));
     const uint32_t dst = d.cstart[c] + rank;
-    if (dst >= (uint32_t)d.n || id >= (uint32_t)d.n) { set_err(d, ERR_INTERNAL); return; }
+    if (dst >= (uint32_t)d.n || id >= (uint32_t)d.n) {
+        set_err_at(d, ERR_INTERNAL, 1, k, dst, id);
+        return;
+    }
     d.S_xv[dst] = xv;
     d.S_id[dst] = id;
     d.slot[id] = dst;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, ui
             fy += (fb + sp) * ey;
         }
     } else {
-        set_err(d, ERR_INTERNAL);
+        set_err_at(d, ERR_INTERNAL, 2, g, id, ps);
     }
     float vx = vbits(xv.z), vy = vbits(xv.w);
     fx -= d.zeta * vx;

@@ -26,12 +26,16 @@ def make_params(L: float, n_beads: int, **kw) -> DpdParams:
 class Sim:
     """One periodic box of N beads (N/2 dimers) on the current CUDA device."""
 
-    def __init__(self, L: float, n_beads: int, stream=None, **params):
+    def __init__(self, L: float, n_beads: int, stream=None, _view=None, **params):
         self.L = self._lib = None
         self._lib = _lib.lib()
         self.params = make_params(L, n_beads, **params)
         self.L = float(L)
         self.n = int(n_beads)
+        self._owned = _view is None
+        if _view is not None:       # a replica of a batch: borrowed handle
+            self._h = _view
+            return
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(int(stream)) if stream else None
         check(self._lib.dpd_create(ctypes.byref(self.params), st, ctypes.byref(h)), "dpd_create")
@@ -138,6 +142,12 @@ class Sim:
         check(self._lib.dpd_profile_step(self._h, ptr(ms)), "dpd_profile_step")
         return ms
 
+    def error_info(self):
+        """(site, v1, v2, v3) of the first failed device check (site 0: none)."""
+        out = np.zeros(4, np.int64)
+        check(self._lib.dpd_error_info(self._h, ptr(out)), "dpd_error_info")
+        return tuple(int(v) for v in out)
+
     def info(self) -> DpdInfo:
         inf = DpdInfo()
         check(self._lib.dpd_get_info(self._h, ctypes.byref(inf)), "dpd_get_info")
@@ -145,7 +155,8 @@ class Sim:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._lib is not None:
-            self._lib.dpd_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._lib.dpd_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,107 @@
+"""The batched persistent kernel advances every replica exactly as the
+single-system path does (same arithmetic), for replicas of uneven box size,
+bead count and parameters; its grid barrier gives up after a bounded wait."""
+import numpy as np
+import pytest
+
+from paper_1310_0998_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+BASE = dict(a=25.0, gamma=4.5, kBT=1.0, rc=1.0, k_bond=100.0, r0=0.5, f_p=1.0, zeta=0.1, dt=0.01)
+
+
+def minimg(d, L):
+    return d - L * np.rint(d / L)
+
+
+def _points():
+    # box sides on the 1/256 grid, uneven sizes, densities and frictions
+    spec = [(24.0, 300, 4.5, 0.1, 1.0), (32.5, 900, 1.0, 0.5, 1.5), (17.25, 150, 20.0, 0.01, 0.5),
+            (40.0, 2000, 0.7, 1.3, 2.0), (9.0, 40, 4.5, 0.0, 0.0), (64.0, 4000, 3.0, 0.05, 1.0)]
+    pts = []
+    for r, (L, nd, g, z, fp) in enumerate(spec):
+        pts.append(dict(BASE, L=L, n_beads=2 * nd, gamma=g, zeta=z, f_p=fp, seed=100 + r, replica=r))
+    return pts
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1310_0998_gb300 import Ensemble, Sim
+    return Ensemble, Sim
+
+
+def test_batch_matches_single_system(mods):
+    Ensemble, Sim = mods
+    pts = _points()
+    states = []
+    with Ensemble(pts) as ens:
+        for r, pt in enumerate(pts):
+            x, _ = synth.dimers(pt["n_beads"] // 2, pt["L"], 0.5, seed=r)
+            v = synth.velocities(pt["n_beads"], 0.5, seed=r + 7)
+            ens.replica(r).set_positions(x, v)
+            states.append((x, v))
+        ens.step(40)
+        ens.sync()
+        got = [ens.replica(r).get_state() for r in range(len(pts))]
+        logs = [ens.replica(r).thermo_log(1, 40) for r in range(len(pts))]
+        info = ens.info()
+    assert info["replicas"] == len(pts) and info["grid"] > 0
+    for r, pt in enumerate(pts):
+        kw = {k: v for k, v in pt.items() if k not in ("L", "n_beads")}
+        with Sim(pt["L"], pt["n_beads"], **kw) as s:
+            s.set_positions(*states[r])
+            s.step(40)
+            xs, vs, fs, st = s.get_state()
+            log = s.thermo_log(1, 40)
+        xb, vb, fb, sb = got[r]
+        assert sb == st == 40
+        assert np.abs(minimg(xb - xs, pt["L"])).max() < 1e-5, r
+        np.testing.assert_allclose(vb, vs, atol=1e-3)
+        np.testing.assert_allclose(logs[r][:, 0], log[:, 0], rtol=1e-4)
+
+
+def test_batch_against_oracle(mods, orc):
+    """One replica of the batch against the FP64 oracle, 100 steps."""
+    Ensemble, _ = mods
+    pts = _points()[:3]
+    L, nd = pts[1]["L"], pts[1]["n_beads"] // 2
+    x, v = synth.dimers(nd, L, 0.5, seed=5)
+    with Ensemble(pts) as ens:
+        ens.init_random(9)
+        ens.replica(1).set_positions(x, v)
+        ens.step(100)
+        xb, _, _, _ = ens.replica(1).get_state()
+    p = pts[1]
+    op = orc.params(L=L, a=p["a"], gamma=p["gamma"], kBT=p["kBT"], rc=p["rc"], kbond=p["k_bond"], r0=p["r0"],
+                    fp=p["f_p"], zeta=p["zeta"], dt=p["dt"], seed=p["seed"], replica=p["replica"])
+    st = orc.State(op, x, v)
+    st.run(100)
+    assert np.abs(minimg(xb - st.x, L)).max() <= 1e-4
+
+
+def test_barrier_timeout_is_reported_and_batch_survives(mods):
+    Ensemble, _ = mods
+    pts = _points()[:2]
+    with Ensemble(pts) as ens:
+        ens.init_random(1)
+        assert ens.barrier_selftest() == -5          # DPD_ERR_TIMEOUT
+        ens.step(5)
+        ens.sync()
+        _, _, _, s = ens.replica(0).get_state()
+        assert s == 5
+
+
+def test_replica_views_are_borrowed(mods):
+    Ensemble, _ = mods
+    from paper_1310_0998_gb300 import _lib
+    pts = _points()[:2]
+    with Ensemble(pts) as ens:
+        ens.init_random(3)
+        view = ens.replica(0)
+        _lib.lib().dpd_destroy(view._h)   # ignored for a replica
+        ens.step(3)
+        ens.sync()
+        assert view.get_state()[3] == 3
