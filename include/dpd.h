@@ -241,6 +241,47 @@ int dpd_batch_barrier_selftest(dpd_batch *b);
 /* Replica count, blocks of the persistent launch, (replica, cell block) items. */
 int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of ensemble statistics (not part of the paper: a model
+ * of this simulator's own outputs).  A deep ensemble of K MLPs
+ * 4 -> 256 -> 256 -> 40 (SiLU hidden layers, linear output), BF16 weights and
+ * activations, FP32 accumulation on the tensor cores, Adam on FP32 master
+ * weights.  Input row: (area fraction, gamma, zeta, f_p) (gamma and zeta
+ * enter as logarithms); output row: 40 statistics (see the binding's
+ * documentation for their order).  Inputs and outputs are standardised with
+ * the training set's mean and standard deviation.  Host pointers.
+ * ------------------------------------------------------------------------ */
+typedef struct sur_ctx sur_ctx;
+
+/* n_members >= 1 MLPs with independent seeded initial weights; max_rows
+ * bounds the rows of any later call. */
+int sur_create(int n_members, int max_rows, uint64_t seed, void *stream, sur_ctx **out);
+void sur_destroy(sur_ctx *s);
+
+/* Replace member weights (FP32 masters; row-major, padded shapes):
+ * W1 [256][16] (input columns 4..15 zero), b1 [256], W2 [256][256], b2 [256],
+ * W3 [48][256] (rows 40..47 zero), b3 [48]. */
+int sur_set_weights(sur_ctx *s, int member, const float *W1, const float *b1, const float *W2, const float *b2,
+                    const float *W3, const float *b3);
+
+/* Standardisation of inputs (after the logarithms) and outputs. */
+int sur_set_scaling(sur_ctx *s, const float mu_x[4], const float sd_x[4], const float mu_y[40], const float sd_y[40]);
+
+/* One forward and backward pass of one member on (X [n][4], Y [n][40]) with
+ * the current scaling: mean squared error of the standardised outputs and
+ * its gradients (shapes as in sur_set_weights; any output may be NULL). */
+int sur_gradients(sur_ctx *s, int member, const float *X, const float *Y, int n, float *loss, float *gW1,
+                  float *gb1, float *gW2, float *gb2, float *gW3, float *gb3);
+
+/* Train every member with Adam (lr) for `epochs` passes over shuffled
+ * minibatches of `batch` rows; sets the scaling from (X, Y) first.
+ * final_loss: mean squared standardised error of the last epoch. */
+int sur_train(sur_ctx *s, const float *X, const float *Y, int n, int epochs, int batch, float lr, float *final_loss);
+
+/* Ensemble mean Y [n][40] and member standard deviation spread [n][40]
+ * (may be NULL), in output units. */
+int sur_predict(sur_ctx *s, const float *X, int n, float *Y, float *spread);
+
 #ifdef __cplusplus
 }
 #endif

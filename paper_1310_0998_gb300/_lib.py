@@ -100,6 +100,13 @@ def _declare(L):
         "dpd_batch_sync": ([vp], c_int),
         "dpd_batch_barrier_selftest": ([vp], c_int),
         "dpd_batch_info": ([vp, P(c_int), P(c_int), P(c_int)], c_int),
+        "sur_create": ([c_int, c_int, u64, vp, P(vp)], c_int),
+        "sur_destroy": ([vp], None),
+        "sur_set_weights": ([vp, c_int, vp, vp, vp, vp, vp, vp], c_int),
+        "sur_set_scaling": ([vp, vp, vp, vp, vp], c_int),
+        "sur_gradients": ([vp, c_int, vp, vp, c_int, P(ctypes.c_float), vp, vp, vp, vp, vp, vp], c_int),
+        "sur_train": ([vp, vp, vp, c_int, c_int, c_int, ctypes.c_float, P(ctypes.c_float)], c_int),
+        "sur_predict": ([vp, vp, c_int, vp, vp], c_int),
     }
     for name, (args, res) in sig.items():
         if hasattr(L, name):
