@@ -170,6 +170,20 @@ int dpd_velocity_field(dpd_ctx *ctx, int M, double eps, double *u, double *n_in)
  * E: host [M/2] (E[0] is k = 1).  FP64 FFT on the device.  Synchronises. */
 int dpd_energy_spectrum(dpd_ctx *ctx, int M, double eps, double *E);
 
+/* The same E(k) as dpd_energy_spectrum (same arguments and output), computed
+ * without allocating any memory.  The paper has no counterpart: this is a
+ * property of this library, for callers that must not allocate mid-run (a
+ * state sized to fill device memory, where a late cudaMalloc fails; a
+ * pipelined run, where cudaMalloc / cudaFree would synchronise the device).
+ * Scratch is one static device array per device of 2,622,464 bytes, so
+ * M <= 256 (M > 256 gives DPD_ERR_INVALID_ARG); the per-agent staging of the
+ * allocating path is fused into the deposit kernel.  The first call on a
+ * device (with that device current) looks up the array's address; make it
+ * before any stream capture.  The array is shared by every context on the
+ * device: calls whose stream work overlaps race on it and return wrong
+ * values, so serialise them.  Synchronises. */
+int dpd_energy_spectrum_noalloc(dpd_ctx *ctx, int M, double eps, double *E);
+
 /* Eqs. (VCF), (spatial01): all agent pairs with COM separation in
  * [b dr, (b+1) dr), b < nbins (nbins dr <= L/2 advised):
  *   g[b] = (<v_a.v_b>_b - |<v>|^2) / (<|v|^2> - |<v>|^2) (global means),

@@ -16,6 +16,7 @@
 // no contraction), so they are reproducible bit for bit off the device.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dpd.h"
@@ -380,3 +381,134 @@ int dpd_velocity_correlation(dpd_ctx *c, double dr, int nbins, double *g, double
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// E(k) with no allocation: dpd_energy_spectrum_noalloc.
+//
+// Which callers cannot allocate, and why.  dpd_energy_spectrum grows a scratch
+// buffer with cudaMalloc on first use (and again when a larger M or box comes
+// along).  Two kinds of caller cannot accept that in the middle of a run: one
+// whose simulation state was sized to fill the device's memory (the largest
+// boxes), where the late cudaMalloc fails; and one that samples E(k) every few
+// hundred steps from inside a pipelined run, where cudaMalloc / cudaFree
+// synchronise the whole device and stall the other streams.  This variant
+// keeps its scratch in one fixed static device array instead.
+//
+// How.  The agent centres of mass and velocities, which the allocating path
+// stages in a per-agent buffer, are recomputed inside the deposit kernel
+// (k_deposit_state, the same IEEE operations as k_agent_com), so the scratch
+// no longer grows with the number of agents; what remains is the grid:
+// per point the window sums of u_x and u_y, the window count and the complex
+// field (5 doubles), plus M/2 shell sums: 2,622,464 bytes at the maximum
+// M = 256.  Larger M is rejected.
+//
+// What must start at zero.  The three window sums and the shell sums are
+// accumulated with atomics; every call clears them (cudaMemsetAsync on the
+// caller's stream) before the deposit.  The field is overwritten in full.
+//
+// Sharing.  There is one array per device, shared by every context on it:
+// two calls whose stream work overlaps (two host threads, or two contexts on
+// different streams) race on it and return wrong values.  Serialise them.
+//
+// Set-up.  The first call on a device, made with that device current, looks up
+// the array's device address with cudaGetSymbolAddress and keeps it for later
+// calls on that device; make that first call before any stream capture.
+// ---------------------------------------------------------------------------
+
+namespace {
+constexpr int NOALLOC_MAX_M = 256;
+constexpr size_t NOALLOC_MAX_GRID = (size_t)NOALLOC_MAX_M * NOALLOC_MAX_M;
+constexpr size_t NOALLOC_DOUBLES = 5 * NOALLOC_MAX_GRID + NOALLOC_MAX_M / 2;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+}  // namespace
+
+static __device__ __align__(256) double g_spectrum_scratch[NOALLOC_DOUBLES];
+
+static double *g_spectrum_scratch_ptr[NOALLOC_MAX_DEVICES];
+static std::mutex g_spectrum_scratch_mu;
+
+// Device address of the static scratch for the current device (set-up on the
+// first call per device).
+static int spectrum_scratch(double **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DPD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_spectrum_scratch_mu);
+    if (!g_spectrum_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
+        if (e != cudaSuccess || !p) return DPD_ERR_CUDA;
+        g_spectrum_scratch_ptr[dev] = (double *)p;
+    }
+    *out = g_spectrum_scratch_ptr[dev];
+    return DPD_OK;
+}
+
+namespace dpd {
+
+// k_agent_com followed by k_deposit for one agent, without staging the
+// centres of mass and velocities in memory.
+__global__ void k_deposit_state(const uint4 *__restrict__ xv, int na, double L, double ulen, double dxg,
+                                double half, int M, double *sx, double *sy, double *cnt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const uint4 h = xv[2 * k], t = xv[2 * k + 1];
+    const double hx = __dmul_rn((double)h.x, ulen), hy = __dmul_rn((double)h.y, ulen);
+    const double tx = __dmul_rn((double)t.x, ulen), ty = __dmul_rn((double)t.y, ulen);
+    const double dx = minimg_d(__dsub_rn(hx, tx), L);
+    const double dy = minimg_d(__dsub_rn(hy, ty), L);
+    double cx = __dadd_rn(tx, __dmul_rn(0.5, dx));
+    double cy = __dadd_rn(ty, __dmul_rn(0.5, dy));
+    cx = __dsub_rn(cx, __dmul_rn(L, floor(__ddiv_rn(cx, L))));
+    cy = __dsub_rn(cy, __dmul_rn(L, floor(__ddiv_rn(cy, L))));
+    const double hvx = (double)__uint_as_float(h.z), hvy = (double)__uint_as_float(h.w);
+    const double tvx = (double)__uint_as_float(t.z), tvy = (double)__uint_as_float(t.w);
+    const double vx = __dmul_rn(0.5, __dadd_rn(hvx, tvx)), vy = __dmul_rn(0.5, __dadd_rn(hvy, tvy));
+    int ix[64], iy[64];
+    const int nx = window_hits(cx, L, dxg, half, M, ix, 64);
+    const int ny = window_hits(cy, L, dxg, half, M, iy, 64);
+    for (int a = 0; a < ny; ++a)
+        for (int b = 0; b < nx; ++b) {
+            const size_t g = (size_t)iy[a] * M + ix[b];
+            atomicAdd(&sx[g], vx);
+            atomicAdd(&sy[g], vy);
+            atomicAdd(&cnt[g], 1.0);
+        }
+}
+
+}  // namespace dpd
+
+extern "C" int dpd_energy_spectrum_noalloc(dpd_ctx *c, int M, double eps, double *E)
+{
+    if (!c || !E || M < 4 || M > NOALLOC_MAX_M || (M & (M - 1))) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    const int na = c->d.n / 2;
+    const double L = c->p.L;
+    if (eps <= 0.0) eps = L * std::sqrt(10.0 / (double)na);
+    if (eps / (L / M) > 56.0) return DPD_ERR_INVALID_ARG;
+    double *scr = nullptr;
+    const int rc = spectrum_scratch(&scr);
+    if (rc) return rc;
+    const size_t MM = (size_t)M * M;
+    double *sx = scr, *sy = sx + MM, *cn = sy + MM;
+    double2 *z = (double2 *)(cn + MM);          // 16-byte aligned: 3 MM doubles, MM even
+    double *dE = (double *)(z + MM);
+    CUO(cudaMemsetAsync(sx, 0, 8 * MM * 3, c->st));
+    CUO(cudaMemsetAsync(dE, 0, 8 * (size_t)(M / 2), c->st));
+    k_deposit_state<<<(na + 127) / 128, 128, 0, c->st>>>(c->d.C_xv, na, L, c->d.ulen_d, L / M, 0.5 * eps, M, sx,
+                                                         sy, cn);
+    k_field_finish<<<(int)((MM + 255) / 256), 256, 0, c->st>>>(sx, sy, cn, (int)MM, z);
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    const size_t sm = 16 * (size_t)M;
+    const int thr = M / 2 < 512 ? M / 2 : 512;
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, 1, M);
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, M, 1);
+    const double M2 = (double)M * (double)M;
+    k_shells<<<(M * M + 255) / 256, 256, 0, c->st>>>(z, M, 0.5 / (M2 * M2), dE);
+    CUO(cudaGetLastError());
+    CUO(cudaMemcpyAsync(E, dE, 8 * (size_t)(M / 2), cudaMemcpyDeviceToHost, c->st));
+    return dpd_internal_latched(c);
+}
