@@ -39,7 +39,7 @@ constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (x ~100 ns)
 
 // Per-system view handed to every kernel by value.
 struct Sys {
-    double Ld, ulen_d;             // L and L / 2^32 in double (state conversion)
+    double Ld, ulen_d, inv_ulen_d; // L, L / 2^32 and 2^32 / L in double (state conversion)
     float L, ulen, inv_ulen, cs;   // ulen = L / 2^32, inv_ulen = 2^32 / L
     int nc, ntx, n, ncells;
     float rc2, inv_rc, a, gamma, sig_r, kbond, r0, fp, zeta, dt, hdtm;

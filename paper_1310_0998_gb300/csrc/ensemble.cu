@@ -223,6 +223,7 @@ static void ens_launch(dpd_batch *b, int nsteps, int final_last)
 static int ens_dispatch_prepare(dpd_batch *b)
 {
     if (b->var == 1) return b->B == 4 ? ens_prepare<4, 1>(b) : b->B == 8 ? ens_prepare<8, 1>(b) : ens_prepare<16, 1>(b);
+    if (b->var == 3) return b->B == 4 ? ens_prepare<4, 3>(b) : b->B == 8 ? ens_prepare<8, 3>(b) : ens_prepare<16, 3>(b);
     return b->B == 4 ? ens_prepare<4, 2>(b) : b->B == 8 ? ens_prepare<8, 2>(b) : ens_prepare<16, 2>(b);
 }
 
@@ -232,6 +233,10 @@ static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last)
         if (b->B == 4) ens_launch<4, 1>(b, nsteps, final_last);
         else if (b->B == 8) ens_launch<8, 1>(b, nsteps, final_last);
         else ens_launch<16, 1>(b, nsteps, final_last);
+    } else if (b->var == 3) {
+        if (b->B == 4) ens_launch<4, 3>(b, nsteps, final_last);
+        else if (b->B == 8) ens_launch<8, 3>(b, nsteps, final_last);
+        else ens_launch<16, 3>(b, nsteps, final_last);
     } else {
         if (b->B == 4) ens_launch<4, 2>(b, nsteps, final_last);
         else if (b->B == 8) ens_launch<8, 2>(b, nsteps, final_last);
@@ -267,7 +272,7 @@ static int ens_build_tables(dpd_batch *b)
     for (int r = 0; r < b->R; ++r) sys[r].cap = cap;
     for (int r = 0; r < b->R; ++r) b->reps[r]->d.cap = cap;
     b->cap = cap;
-    b->smem = force_smem(b->B, cap, false);
+    b->smem = force_smem(b->B, b->var, cap, false);
     b->n_scat = (int)scat.size();
     b->n_tiles = (int)tiles.size();
     if (b->pool) cudaFree(b->pool);
@@ -288,7 +293,7 @@ static int ens_build_tables(dpd_batch *b)
     for (int r = 0; r < b->R; ++r) {
         dpd_ctx *c = b->reps[r];
         c->smem = b->smem;
-        const int rc = set_force_smem(c->B, cap);
+        const int rc = set_force_smem(c->B, b->var, cap);
         if (rc) return rc;
     }
     int rc = ens_dispatch_prepare(b);

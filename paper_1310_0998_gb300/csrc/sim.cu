@@ -36,13 +36,16 @@ __global__ void k_bin(Sys d)
 
 __global__ void k_set_step(Sys d, long long s) { *d.step = s; }
 
-// Double position -> fixed point: wrap into [0, L), round to the nearest unit
-// of L / 2^32 (exact for positions already on that grid).
+// Double position -> fixed point: round x 2^32 / L to the nearest integer and
+// keep it modulo 2^32, which is the wrap into [0, L) because L is exactly 2^32
+// units.  One multiply instead of divides (FP64 is a slow pipe on this part);
+// for a position already on the grid the product is within 2^-20 of an
+// integer, so the result is exact.  |x| beyond 2^20 L is refused.
 __device__ __forceinline__ uint32_t to_fixed(const Sys &d, double x, bool &ok)
 {
-    if (!isfinite(x)) { ok = false; return 0u; }
-    const double xr = x - d.Ld * floor(x / d.Ld);
-    return (uint32_t)(unsigned long long)llrint(xr / d.ulen_d);
+    const double u = x * d.inv_ulen_d;
+    if (!(fabs(u) < 4503599627370496.0)) { ok = false; return 0u; }   // 2^52 units; false for NaN
+    return (uint32_t)(unsigned long long)llrint(u);
 }
 
 // Upload: positions (double [N][2]) and velocities (float [N][2]) in id order.
@@ -188,7 +191,7 @@ int validate(const dpd_params *p)
         return DPD_ERR_INVALID_ARG;
     if (p->n_beads < 2 || (p->n_beads & 1) || p->n_beads >= (1ll << 31)) return DPD_ERR_INVALID_ARG;
     if (!(p->tile == 0 || p->tile == 4 || p->tile == 8 || p->tile == 16)) return DPD_ERR_INVALID_ARG;
-    if (p->variant < 0 || p->variant > 2) return DPD_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 3) return DPD_ERR_INVALID_ARG;
     if (p->noise < 0 || p->noise > 1) return DPD_ERR_INVALID_ARG;
     const int nc = n_cells_side(p->L, p->rc);
     if (nc < 3 || (double)nc * nc >= 2.0e9) return DPD_ERR_INVALID_ARG;
@@ -224,6 +227,7 @@ void fill_geometry(Sys &d, const dpd_params *p, int B)
     const int nc = n_cells_side(p->L, p->rc);
     d.Ld = p->L;
     d.ulen_d = std::ldexp(p->L, -32);
+    d.inv_ulen_d = std::ldexp(1.0, 32) / p->L;
     d.L = (float)p->L;
     d.ulen = (float)d.ulen_d;
     d.inv_ulen = (float)(std::ldexp(1.0, 32) / p->L);
@@ -247,8 +251,15 @@ int tile_capacity(const dpd_params *p, int B)
     return std::min(std::max(cap, 256), 4096);   // queue entries pack bead slots in 12 bits
 }
 
-size_t force_smem(int B, int cap, bool count)
+size_t force_smem(int B, int var, int cap, bool count)
 {
+    if (var == 3) {
+        switch (B) {
+            case 4: return TilePlanG<4>::bytes(cap, TILE_THREADS, count);
+            case 8: return TilePlanG<8>::bytes(cap, TILE_THREADS, count);
+            default: return TilePlanG<16>::bytes(cap, TILE_THREADS, count);
+        }
+    }
     switch (B) {
         case 4: return TilePlan<4>::bytes(cap, TILE_THREADS, count);
         case 8: return TilePlan<8>::bytes(cap, TILE_THREADS, count);
@@ -275,6 +286,8 @@ static int set_force_attrs(int smax)
     if (!rc) rc = set_dyn_limit(k_force<B, true, 1>, smax);
     if (!rc) rc = set_dyn_limit(k_force<B, false, 2>, smax);
     if (!rc) rc = set_dyn_limit(k_force<B, true, 2>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, false, 3>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, true, 3>, smax);
     return rc;
 }
 
@@ -286,10 +299,10 @@ int max_dynamic_smem()
     return smax;
 }
 
-int set_force_smem(int B, int cap)
+int set_force_smem(int B, int var, int cap)
 {
     const int smax = max_dynamic_smem();
-    if ((int)force_smem(B, cap, true) > smax) return DPD_ERR_INVALID_ARG;
+    if ((int)force_smem(B, var, cap, true) > smax) return DPD_ERR_INVALID_ARG;
     int rc = set_force_attrs<4>(smax);
     if (!rc) rc = set_force_attrs<8>(smax);
     if (!rc) rc = set_force_attrs<16>(smax);
@@ -300,7 +313,7 @@ template <int B, int VAR>
 static void launch_force_t(const Sys &d, cudaStream_t st, size_t smem, int flags, bool count)
 {
     const int ntiles = d.ntx * d.ntx;
-    if (count) k_force<B, true, VAR><<<ntiles, TILE_THREADS, force_smem(B, d.cap, true), st>>>(d, flags);
+    if (count) k_force<B, true, VAR><<<ntiles, TILE_THREADS, force_smem(B, VAR, d.cap, true), st>>>(d, flags);
     else k_force<B, false, VAR><<<ntiles, TILE_THREADS, smem, st>>>(d, flags);
 }
 
@@ -311,6 +324,12 @@ void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t sme
             case 4: launch_force_t<4, 1>(d, st, smem, flags, count); break;
             case 8: launch_force_t<8, 1>(d, st, smem, flags, count); break;
             default: launch_force_t<16, 1>(d, st, smem, flags, count); break;
+        }
+    } else if (var == 3) {
+        switch (B) {
+            case 4: launch_force_t<4, 3>(d, st, smem, flags, count); break;
+            case 8: launch_force_t<8, 3>(d, st, smem, flags, count); break;
+            default: launch_force_t<16, 3>(d, st, smem, flags, count); break;
         }
     } else {
         switch (B) {
@@ -451,10 +470,10 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     fill_geometry(d, p, c->B);
     fill_physics(d, p);
     d.cap = tile_capacity(p, c->B);
-    c->smem = force_smem(c->B, d.cap, false);
-    if (force_smem(c->B, d.cap, true) > 200 * 1024) {
-        d.cap = (int)((200 * 1024 - force_smem(c->B, 0, true)) / 33) & ~31;
-        c->smem = force_smem(c->B, d.cap, false);
+    c->smem = force_smem(c->B, c->var, d.cap, false);
+    if (force_smem(c->B, c->var, d.cap, true) > 200 * 1024) {
+        d.cap = (int)((200 * 1024 - force_smem(c->B, c->var, 0, true)) / 35) & ~31;
+        c->smem = force_smem(c->B, c->var, d.cap, false);
     }
     c->nscan = (d.ncells + SCAN_TILE - 1) / SCAN_TILE;
     const size_t n = (size_t)d.n, nce = (size_t)d.ncells;
@@ -500,7 +519,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     d.scan_status = (unsigned long long *)(b + o_ss);
     d.scan_ticket = (unsigned long long *)(b + o_tk);
     if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess ||
-        (rc = set_force_smem(c->B, d.cap)) != DPD_OK) {
+        (rc = set_force_smem(c->B, c->var, d.cap)) != DPD_OK) {
         dpd_destroy(c);
         return rc ? rc : DPD_ERR_CUDA;
     }

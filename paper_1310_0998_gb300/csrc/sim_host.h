@@ -11,11 +11,11 @@ int validate(const dpd_params *p);
 void fill_physics(Sys &d, const dpd_params *p);
 void fill_geometry(Sys &d, const dpd_params *p, int B);
 int tile_capacity(const dpd_params *p, int B);
-size_t force_smem(int B, int cap, bool count);
+size_t force_smem(int B, int var, int cap, bool count);
 void launch_iteration(const Sys &d, int B, int var, cudaStream_t st, int nscan, size_t smem, int flags, bool count);
 void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t smem, int flags, bool count);
 void launch_scatter(const Sys &d, int B, cudaStream_t st);
-int set_force_smem(int B, int cap);
+int set_force_smem(int B, int var, int cap);
 int max_dynamic_smem();
 void launch_bin(const Sys &d, int B, cudaStream_t st);
 void launch_kick_bin(const Sys &d, int B, cudaStream_t st);

@@ -433,6 +433,348 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
     if (lane < qn) queue_eval<COUNT>(d, q[lane], s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lo, s_hi);
 }
 
+// Global-memory path for a tile whose beads do not fit in shared memory: one
+// thread per owned bead, pairs from both sides (no Newton-3), same arithmetic.
+template <int B, bool COUNT>
+__device__ void force_tile_global(const Sys &d, uint32_t g0, int n_own, uint32_t s_lo, uint32_t s_hi, int flags,
+                                  Thermo3 &th)
+{
+    const uint32_t n = (uint32_t)d.n;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    if (tid == 0) atomicAdd(d.ovf, 1ull);
+    for (int k = tid; k < n_own; k += NT) {
+        const int g = (int)g0 + k;
+        const uint4 xv = d.S_xv[g];
+        const float vix = vbits(xv.z), viy = vbits(xv.w);
+        const uint32_t idi = d.S_id[g], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
+        const int cx = cell_coord(d, xv.x), cy = cell_coord(d, xv.y);
+        float fx = 0.f, fy = 0.f;
+        uint32_t cnt = 0;
+        for (int oy_ = -1; oy_ <= 1; ++oy_)
+            for (int ox_ = -1; ox_ <= 1; ++ox_) {
+                int ncx = cx + ox_, ncy = cy + oy_;
+                ncx += (ncx < 0) ? d.nc : ((ncx >= d.nc) ? -d.nc : 0);
+                ncy += (ncy < 0) ? d.nc : ((ncy >= d.nc) ? -d.nc : 0);
+                const int gc = cell_of<B>(d, ncx, ncy);
+                const uint32_t b = min(d.cstart[gc], n), e = min(max(d.cstart[gc + 1], b), n);
+                for (uint32_t q = b; q < e; ++q) {
+                    if (q == (uint32_t)g) continue;
+                    const uint32_t idj = d.S_id[q];
+                    if (idj == pid) continue;
+                    const uint4 xj = d.S_xv[q];
+                    const float dx = mdiff(d, xv.x, xj.x);
+                    const float dy = mdiff(d, xv.y, xj.y);
+                    const float r2 = dx * dx + dy * dy;
+                    if (r2 < d.rc2 && r2 > 0.f) {
+                        float ex, ey;
+                        const float F = dpd_pair_scalar(d, dx, dy, vix - vbits(xj.z), viy - vbits(xj.w), idi,
+                                                        idj, s_lo, s_hi, r2, ex, ey);
+                        fx += F * ex;
+                        fy += F * ey;
+                        if (COUNT) ++cnt;
+                    }
+                }
+            }
+        if (COUNT && d.pcnt) d.pcnt[idi] = cnt;
+        integrate_bead<B>(d, g, xv, idi, fx, fy, flags, th);
+    }
+}
+
+// ------------------------------------------------- grid-order tile (VAR 3) --
+// The tile's owned and halo cells are staged in shared memory in the row-major
+// order of the local (B+2) x (B+2) cell grid, with raw fixed-point positions,
+// so every row of the local grid is one contiguous bead range and a pair
+// separation is the wrapped integer difference of two positions (exact) times
+// the unit.  The forward half-stencil of an owned cell (own cell after the
+// bead, E, and NW..NE) is then two ranges instead of five; a cell on the tile
+// edge adds at most three ranges of halo cells behind it (W, and SW..SE or
+// parts of that row).  Each lane walks the candidates of one owned bead at a
+// time, CPR candidates per round; pairs inside r_c go through the warp's pair
+// queue as in variant 2 (Newton-3 when the partner is owned).
+template <int B>
+struct TilePlanG {
+    static constexpr int W = B + 2;
+    static constexpr int NCL = W * W;
+    static constexpr int NINT = 3 * NCL + 1 + 4;   // counts, begins (+1), global sources, misc
+    static constexpr int CPR = 4;                   // candidates per lane per round
+    static constexpr int QLEN = 32 * (CPR + 1);     // queue entries per warp
+    static __host__ __device__ size_t red_off() { return ((size_t)NINT * 4 + 7) & ~size_t(7); }
+    static __host__ __device__ size_t bead_off(int nthreads)
+    {
+        return (red_off() + sizeof(double) * 3 * (size_t)(nthreads / 32 + 1) + 15) & ~size_t(15);
+    }
+    // per staged bead: position 8, velocity 8, id 4, fx 4, fy 4, (count 4),
+    // owned-bead slot 2, owned flag 1
+    static __host__ __device__ size_t bead_bytes(bool count) { return count ? 35 : 31; }
+    static __host__ __device__ size_t queue_off(int cap, int nthreads, bool count)
+    {
+        return (bead_off(nthreads) + (size_t)cap * bead_bytes(count) + 15) & ~size_t(15);
+    }
+    static __host__ __device__ size_t bytes(int cap, int nthreads, bool count)
+    {
+        return queue_off(cap, nthreads, count) + sizeof(uint32_t) * QLEN * (size_t)(nthreads / 32);
+    }
+};
+
+template <bool COUNT>
+__device__ __forceinline__ void queue_eval_g(const Sys &d, uint32_t code, const uint2 *s_X, const float2 *s_vel,
+                                             const uint32_t *s_id, const unsigned char *s_own, float *s_fx,
+                                             float *s_fy, uint32_t *s_cnt, uint32_t s_lo, uint32_t s_hi)
+{
+    const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
+    const uint2 xi = s_X[k], xj = s_X[j];
+    const float2 vi = s_vel[k], vj = s_vel[j];
+    const float dx = mdiff(d, xi.x, xj.x), dy = mdiff(d, xi.y, xj.y);
+    const float r2 = dx * dx + dy * dy;
+    float ex, ey;
+    const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, s_id[k], s_id[j], s_lo, s_hi, r2, ex, ey);
+    const float gx = F * ex, gy = F * ey;
+    atomicAdd(&s_fx[k], gx);
+    atomicAdd(&s_fy[k], gy);
+    if (COUNT) atomicAdd(&s_cnt[k], 1u);
+    if (s_own[j]) {
+        atomicAdd(&s_fx[j], -gx);
+        atomicAdd(&s_fy[j], -gy);
+        if (COUNT) atomicAdd(&s_cnt[j], 1u);
+    }
+}
+
+template <int B, bool COUNT>
+__device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int y0, int tw, const int *s_lbeg,
+                                           const uint2 *s_X, const float2 *s_vel, const uint32_t *s_id,
+                                           const unsigned char *s_own, const uint16_t *s_oslot, float *s_fx,
+                                           float *s_fy, uint32_t *s_cnt, volatile uint32_t *q, int *s_next,
+                                           uint32_t s_lo, uint32_t s_hi)
+{
+    using TP = TilePlanG<B>;
+    constexpr int W = TP::W, CPR = TP::CPR;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int j = 0, je = 0, stage = 5, lc = 0, lx = 0, ly = 0, si = 0;
+    uint32_t Xi = 0, Yi = 0, pid = 0;
+    bool more = true;
+    int qn = 0;   // warp-uniform queue length
+    while (true) {
+        bool have = j < je;
+        if (!have && more) {
+            if (stage >= 5) {
+                const int k = atomicAdd(s_next, 1);
+                if (k >= n_own) {
+                    more = false;
+                } else {
+                    si = s_oslot[k];
+                    const uint2 x = s_X[si];
+                    Xi = x.x;
+                    Yi = x.y;
+                    pid = d.excl ? (s_id[si] ^ 1u) : 0xffffffffu;
+                    lx = cell_coord(d, Xi) - x0;
+                    ly = cell_coord(d, Yi) - y0;
+                    lx += lx < -1 ? d.nc : 0;   // a tile never spans the box, so one wrap at most
+                    ly += ly < -1 ? d.nc : 0;
+                    lc = (ly + 1) * W + lx + 1;
+                    stage = 0;
+                }
+            }
+            // next non-empty range of this bead (stages 0..4)
+            while (more && stage < 5 && !have) {
+                int b = 0, e = 0;
+                if (stage == 0) {          // W, when it is a halo cell
+                    if (lx == 0) { b = s_lbeg[lc - 1]; e = s_lbeg[lc]; }
+                } else if (stage == 1) {   // own cell after the bead, then E
+                    b = si + 1;
+                    e = s_lbeg[lc + 2];
+                } else if (stage == 2) {   // NW, N, NE
+                    b = s_lbeg[lc + W - 1];
+                    e = s_lbeg[lc + W + 2];
+                } else if (stage == 3) {   // the row below: all of it, or SW
+                    if (ly == 0) { b = s_lbeg[lc - W - 1]; e = s_lbeg[lc - W + 2]; }
+                    else if (lx == 0) { b = s_lbeg[lc - W - 1]; e = s_lbeg[lc - W]; }
+                } else {                   // SE on the right edge
+                    if (ly != 0 && lx == tw - 1) { b = s_lbeg[lc - W + 1]; e = s_lbeg[lc - W + 2]; }
+                }
+                ++stage;
+                j = b;
+                je = e;
+                have = j < je;
+            }
+        }
+        if (!__any_sync(FULL, have || more)) break;
+        bool p[CPR];
+        uint32_t c[CPR];
+#pragma unroll
+        for (int u = 0; u < CPR; ++u) {
+            p[u] = false;
+            c[u] = 0u;
+            if (j < je) {
+                const uint2 xj = s_X[j];
+                const float dx = mdiff(d, Xi, xj.x), dy = mdiff(d, Yi, xj.y);
+                const float r2 = dx * dx + dy * dy;
+                p[u] = (r2 < d.rc2) & (r2 > 0.f) & (s_id[j] != pid);
+                c[u] = (uint32_t)si | ((uint32_t)j << 12);
+                ++j;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CPR; ++u) {
+            const unsigned m = __ballot_sync(FULL, p[u]);
+            if (p[u]) q[qn + __popc(m & lt)] = c[u];
+            qn += __popc(m);
+        }
+        __syncwarp();
+        while (qn >= 32) {
+            // evaluate the oldest 32 entries, move the rest (< 32 CPR) to the front
+            const uint32_t mine = q[lane];
+            uint32_t carry[CPR];
+#pragma unroll
+            for (int u = 0; u < CPR; ++u) carry[u] = q[32 * (u + 1) + lane];
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < CPR; ++u)
+                if (lane + 32 * u < qn - 32) q[lane + 32 * u] = carry[u];
+            qn -= 32;
+            __syncwarp();
+            queue_eval_g<COUNT>(d, mine, s_X, s_vel, s_id, s_own, s_fx, s_fy, s_cnt, s_lo, s_hi);
+        }
+    }
+    __syncwarp();
+    if (lane < qn) queue_eval_g<COUNT>(d, q[lane], s_X, s_vel, s_id, s_own, s_fx, s_fy, s_cnt, s_lo, s_hi);
+}
+
+template <int B, bool COUNT>
+__device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *smem, Thermo3 &th)
+{
+    using TP = TilePlanG<B>;
+    constexpr int W = TP::W;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    int *s_lcnt = (int *)smem;
+    int *s_lbeg = s_lcnt + TP::NCL;
+    int *s_lsrc = s_lbeg + TP::NCL + 1;
+    int *s_sc = s_lsrc + TP::NCL;
+    const int cap = d.cap;
+    uint2 *s_X = (uint2 *)(smem + TP::bead_off(NT));
+    float2 *s_vel = (float2 *)(s_X + cap);
+    uint32_t *s_id = (uint32_t *)(s_vel + cap);
+    float *s_fx = (float *)(s_id + cap);
+    float *s_fy = s_fx + cap;
+    uint32_t *s_cnt = (uint32_t *)(s_fy + cap);                       // COUNT only
+    uint16_t *s_oslot = (uint16_t *)(COUNT ? (void *)(s_cnt + cap) : (void *)s_cnt);
+    unsigned char *s_own = (unsigned char *)(s_oslot + cap);
+
+    const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
+    const int x0 = tx * B, y0 = ty * B;
+    const int tw = min(B, d.nc - x0), th_ = min(B, d.nc - y0);
+    const int base = y0 * d.nc + x0 * th_;
+    const uint32_t n = (uint32_t)d.n;
+    const long long step = *d.step;
+    const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
+    const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+    const uint32_t g0 = min(d.cstart[base], n);
+    const uint32_t g1 = max(g0, min(d.cstart[base + tw * th_], n));
+    const int n_own = (int)(g1 - g0);
+
+    // bead counts and global sources of the local grid (cells past the halo
+    // of a ragged tile stay empty)
+    for (int c = tid; c < TP::NCL; c += NT) {
+        const int ly = c / W - 1, lx = c - (ly + 1) * W - 1;
+        int cnt = 0, src = 0;
+        if (lx <= tw && ly <= th_) {
+            if (lx >= 0 && lx < tw && ly >= 0 && ly < th_) {
+                const int oc = ly * tw + lx;
+                const uint32_t b = min(max(d.cstart[base + oc], g0), g1), e = min(max(d.cstart[base + oc + 1], b), g1);
+                src = (int)b;
+                cnt = (int)(e - b);
+            } else {
+                int cx = x0 + lx, cy = y0 + ly;
+                cx += cx < 0 ? d.nc : (cx >= d.nc ? -d.nc : 0);
+                cy += cy < 0 ? d.nc : (cy >= d.nc ? -d.nc : 0);
+                const int gc = cell_of<B>(d, cx, cy);
+                const uint32_t b = min(d.cstart[gc], n), e = min(max(d.cstart[gc + 1], b), n);
+                src = (int)b;
+                cnt = (int)(e - b);
+            }
+        }
+        s_lcnt[c] = cnt;
+        s_lsrc[c] = src;
+    }
+    __syncthreads();
+    if (tid < 32) {   // exclusive scan of the counts in grid order
+        constexpr int PER = (TP::NCL + 31) / 32;
+        int v[PER];
+        int sum = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int c = tid * PER + i;
+            v[i] = c < TP::NCL ? s_lcnt[c] : 0;
+            sum += v[i];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += t;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int c = tid * PER + i;
+            if (c < TP::NCL) s_lbeg[c] = run;
+            run += v[i];
+        }
+        if (tid == 31) {
+            s_lbeg[TP::NCL] = incl;
+            s_sc[0] = incl;
+            s_sc[1] = 0;   // next owned bead for the pair walk
+        }
+    }
+    __syncthreads();
+    const int total = s_sc[0];
+
+    if (total <= cap) {
+        // ---- stage every bead of the local grid: slot s lies in the last
+        // cell whose begin is <= s
+        for (int s = tid; s < total; s += NT) {
+            int lo = 0, hi = TP::NCL - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_lbeg[mid] <= s) lo = mid; else hi = mid - 1;
+            }
+            const int c = lo;
+            const int ly = c / W - 1, lx = c - (ly + 1) * W - 1;
+            const bool owned = lx >= 0 && lx < tw && ly >= 0 && ly < th_;
+            const uint32_t g = min((uint32_t)(s_lsrc[c] + (s - s_lbeg[c])), n - 1);
+            const uint4 xv = d.S_xv[g];
+            s_X[s] = make_uint2(xv.x, xv.y);
+            s_vel[s] = make_float2(vbits(xv.z), vbits(xv.w));
+            s_id[s] = d.S_id[g];
+            s_fx[s] = 0.f;
+            s_fy[s] = 0.f;
+            if (COUNT) s_cnt[s] = 0u;
+            s_own[s] = owned ? 1 : 0;
+            if (owned) s_oslot[g - g0] = (uint16_t)s;
+        }
+        __syncthreads();
+
+        pairs_grid<B, COUNT>(d, n_own, x0, y0, tw, s_lbeg, s_X, s_vel, s_id, s_own, s_oslot, s_fx, s_fy, s_cnt,
+                             (uint32_t *)(smem + TP::queue_off(cap, NT, COUNT)) + TP::QLEN * (tid >> 5), s_sc + 1,
+                             s_lo, s_hi);
+        __syncthreads();
+
+        // ---- integrate owned beads (state read back from shared memory)
+        for (int k = tid; k < n_own; k += NT) {
+            const int s = s_oslot[k];
+            const uint2 x = s_X[s];
+            const float2 v = s_vel[s];
+            const uint32_t id = s_id[s];
+            if (COUNT && d.pcnt) d.pcnt[id] = s_cnt[s];
+            integrate_bead<B>(d, (int)g0 + k, make_uint4(x.x, x.y, fbits(v.x), fbits(v.y)), id, s_fx[s], s_fy[s],
+                              flags, th);
+        }
+    } else {
+        force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
+    }
+}
+
 // Fused force + integrate for one tile.  Thread-per-owned-bead pair search:
 // pairs inside the tile are taken once (Newton-3 through shared-memory
 // atomics on the partner's slot), pairs with halo beads are taken from the
@@ -443,6 +785,10 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
 template <int B, bool COUNT, int VAR>
 __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *smem, Thermo3 &th)
 {
+    if constexpr (VAR == 3) {
+        force_tile_g<B, COUNT>(d, tile, flags, smem, th);
+        return;
+    }
     using TP = TilePlan<B>;
     const int NT = blockDim.x, tid = threadIdx.x;
     int *s_cbeg = (int *)smem;
@@ -593,44 +939,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             integrate_bead<B>(d, g, xv, id, s_fx[k], s_fy[k], flags, th);
         }
     } else {
-        // ---- global-memory path for an over-full tile (one-sided pairs)
-        if (tid == 0) atomicAdd(d.ovf, 1ull);
-        for (int k = tid; k < n_own; k += NT) {
-            const int g = (int)g0 + k;
-            const uint4 xv = d.S_xv[g];
-            const float vix = vbits(xv.z), viy = vbits(xv.w);
-            const uint32_t idi = d.S_id[g], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
-            const int cx = cell_coord(d, xv.x), cy = cell_coord(d, xv.y);
-            float fx = 0.f, fy = 0.f;
-            uint32_t cnt = 0;
-            for (int oy_ = -1; oy_ <= 1; ++oy_)
-                for (int ox_ = -1; ox_ <= 1; ++ox_) {
-                    int ncx = cx + ox_, ncy = cy + oy_;
-                    ncx += (ncx < 0) ? d.nc : ((ncx >= d.nc) ? -d.nc : 0);
-                    ncy += (ncy < 0) ? d.nc : ((ncy >= d.nc) ? -d.nc : 0);
-                    const int gc = cell_of<B>(d, ncx, ncy);
-                    const uint32_t b = min(d.cstart[gc], n), e = min(max(d.cstart[gc + 1], b), n);
-                    for (uint32_t q = b; q < e; ++q) {
-                        if (q == (uint32_t)g) continue;
-                        const uint32_t idj = d.S_id[q];
-                        if (idj == pid) continue;
-                        const uint4 xj = d.S_xv[q];
-                        const float dx = mdiff(d, xv.x, xj.x);
-                        const float dy = mdiff(d, xv.y, xj.y);
-                        const float r2 = dx * dx + dy * dy;
-                        if (r2 < d.rc2 && r2 > 0.f) {
-                            float ex, ey;
-                            const float F = dpd_pair_scalar(d, dx, dy, vix - vbits(xj.z), viy - vbits(xj.w), idi,
-                                                            idj, s_lo, s_hi, r2, ex, ey);
-                            fx += F * ex;
-                            fy += F * ey;
-                            if (COUNT) ++cnt;
-                        }
-                    }
-                }
-            if (COUNT && d.pcnt) d.pcnt[idi] = cnt;
-            integrate_bead<B>(d, g, xv, idi, fx, fy, flags, th);
-        }
+        force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
     }
 }
 

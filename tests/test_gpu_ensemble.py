@@ -33,9 +33,10 @@ def mods():
     return Ensemble, Sim
 
 
-def test_batch_matches_single_system(mods):
+@pytest.mark.parametrize("variant", [2, 3])
+def test_batch_matches_single_system(mods, variant):
     Ensemble, Sim = mods
-    pts = _points()
+    pts = [dict(p, variant=variant) for p in _points()]
     states = []
     with Ensemble(pts) as ens:
         for r, pt in enumerate(pts):

@@ -69,7 +69,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("L,nd,tile,seed", CASES)
 def test_setup_force_parity(Sim, orc, L, nd, tile, seed, variant):
     x, _ = synth.dimers(nd, L, 0.5, seed=seed)
@@ -96,7 +96,7 @@ def test_gaussian_noise_and_no_exclusion(Sim, orc):
     force_check(f, fo)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("L,nd,tile,seed", CASES[:4])
 def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed, variant):
     x, _ = synth.dimers(nd, L, 0.5, seed=seed)
@@ -112,11 +112,12 @@ def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed, variant):
     assert abs(int(tot) - toto) <= int(amb.sum())
 
 
-def test_trajectory_parity_c1_100_steps(Sim, orc):
+@pytest.mark.parametrize("variant", [2, 3])
+def test_trajectory_parity_c1_100_steps(Sim, orc, variant):
     """C1: 512 dimers, L = 32, seed 0: positions after 100 steps."""
     L, nd = 32.0, 512
     x, v = synth.dimers(nd, L, 0.5, seed=0)
-    with Sim(L, 2 * nd, **sim_kw(seed=0)) as s:
+    with Sim(L, 2 * nd, **sim_kw(seed=0, variant=variant)) as s:
         s.set_positions(x, v)
         s.step(100)
         xg, vg, f, step = s.get_state()
@@ -170,6 +171,29 @@ def test_restart_from_full_state(Sim):
     np.testing.assert_array_equal(fr, fm)
     assert sr == 20 and sa == sb == 50
     assert np.abs(minimg(xa - xb, L)).max() < 1e-5
+
+
+@pytest.mark.parametrize("L", [24.0, 37.0, 333.25])
+def test_upload_wraps_periodic_images_exactly(Sim, L):
+    """Positions given as periodic images (x + m L, m = -3..2) upload to the
+    same fixed-point state: the round trip returns the wrapped grid values
+    bit for bit, including points on the box edge."""
+    nd = 200
+    x, v = synth.dimers(nd, L, 0.5, seed=11)
+    u = L / 2.0 ** 32
+    x[:4] = [[0.0, 0.0], [L - u, u], [0.0, L / 2], [L / 3, L - u]]   # box edges and corners
+    x = synth.on_grid(x, L)
+    f = np.zeros_like(v)
+    rng = np.random.default_rng(3)
+    shift = rng.integers(-3, 3, size=x.shape).astype(np.float64) * L
+    with Sim(L, 2 * nd, **sim_kw(seed=1)) as s:
+        s.set_state(x, v, f, 5)
+        x0, v0, _, _ = s.get_state()
+        s.set_state(x + shift, v, f, 5)
+        x1, v1, _, _ = s.get_state()
+    np.testing.assert_array_equal(x0, x)
+    np.testing.assert_array_equal(x1, x0)
+    np.testing.assert_array_equal(v1, v0)
 
 
 def test_momentum_conserved_without_drag_and_propulsion(Sim):
