@@ -135,7 +135,7 @@ __global__ void k_kick_bin(Sys d)
 }
 
 template <int B, bool COUNT, int VAR>
-__global__ void __launch_bounds__(TILE_THREADS, 6) k_force(Sys d, int flags)
+__global__ void __launch_bounds__(TILE_THREADS, 10) k_force(Sys d, int flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Thermo3 th{0.f, 0.f, 0.f};
@@ -244,9 +244,11 @@ int tile_capacity(const dpd_params *p, int B)
     const double cs = p->L / nc;
     const double rho = (double)p->n_beads / (p->L * p->L);
     const double mean = rho * ((B + 2) * cs) * ((B + 2) * cs);
-    // mean staged population plus a wide margin for density fluctuations;
-    // a tile above it takes the (slower, exact) global-memory path
-    int cap = (int)std::ceil(1.5 * mean + 8.0 * std::sqrt(mean) + 64.0);
+    // mean staged population plus a margin for density fluctuations, kept
+    // small enough for ten resident tiles per SM at density 3; a tile above it
+    // takes the (slower, exact) global-memory path, and a context that sees
+    // such tiles grows its capacity at the next synchronising call
+    int cap = (int)std::ceil(1.3 * mean + 8.0 * std::sqrt(mean) + 32.0);
     cap = (cap + 31) & ~31;
     return std::min(std::max(cap, 256), 4096);   // queue entries pack bead slots in 12 bits
 }
@@ -420,12 +422,37 @@ static int ensure_graphs(dpd_ctx *c)
     return DPD_OK;
 }
 
+constexpr int H_PIN_STATUS = 510;   // h_pin holds 512 doubles; [510], [511]: error flag, overflow count
+
+// A tile that did not fit in shared memory ran the global-memory path: raise
+// the capacity by a quarter (within the shared-memory limit) and re-capture
+// the step graphs at the next dpd_step.
+static void grow_capacity(dpd_ctx *c)
+{
+    int cap = std::min(4096, ((c->d.cap * 5 / 4) + 31) & ~31);
+    while (cap > c->d.cap && force_smem(c->B, c->var, cap, true) > 200 * 1024) cap -= 32;
+    if (cap <= c->d.cap) return;
+    c->d.cap = cap;
+    c->smem = force_smem(c->B, c->var, cap, false);
+    free_graphs(c);
+}
+
 int dpd_internal_latched(dpd_ctx *c)
 {
+    // the status words use their own slots at the end of the pinned buffer so
+    // that a caller's values staged at its start (thermo_entry) survive
     int e = 0;
-    CU(cudaMemcpyAsync(c->h_pin, c->d.err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    unsigned long long ovf = 0;
+    double *st = c->h_pin + H_PIN_STATUS;
+    CU(cudaMemcpyAsync(st, c->d.err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(st + 1, c->d.ovf, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
-    std::memcpy(&e, c->h_pin, sizeof(int));
+    std::memcpy(&e, st, sizeof(int));
+    std::memcpy(&ovf, st + 1, sizeof(ovf));
+    if (ovf > c->ovf_seen) {
+        c->ovf_seen = ovf;
+        if (!c->batch_owned) grow_capacity(c);
+    }
     if (e & ERR_NONFINITE) return DPD_ERR_NONFINITE;
     if (e & ERR_TIMEOUT) return DPD_ERR_TIMEOUT;
     if (e & ERR_INTERNAL) return DPD_ERR_INTERNAL;

@@ -40,6 +40,7 @@ struct dpd_ctx {
     double *h_pin = nullptr;        // small pinned staging (thermo, scalars)
     void *obs = nullptr;            // observables scratch (observables.cu)
     void *stage = nullptr;          // 32 B/bead staging for host state transfers
+    unsigned long long ovf_seen = 0;  // overflowed tiles already answered by a larger capacity
 };
 
 int dpd_internal_latched(dpd_ctx *c);

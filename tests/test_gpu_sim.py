@@ -147,6 +147,11 @@ def test_thermo_fp64_reductions(Sim):
         np.testing.assert_allclose(s.temperature(), 2 * ke / (2 * 2 * nd - 2), rtol=1e-6)
         log = s.thermo_log(1, 5)
         np.testing.assert_allclose(log[-1, 0], ke, rtol=1e-6)
+        # the scalar getters and the log read the same FP64 ring entry: equal
+        # bit for bit (a status word staged over the entry would show here)
+        assert s.kinetic_energy() == log[-1, 0]
+        assert tuple(s.momentum()) == (log[-1, 1], log[-1, 2])
+        assert s.temperature() == log[-1, 3]
 
 
 def test_restart_from_full_state(Sim):
@@ -265,6 +270,40 @@ def test_nonfinite_state_is_reported(Sim):
         with pytest.raises(DpdError) as e:
             s.set_positions(np.where(np.arange(2 * nd)[:, None] == 5, np.inf, x), v)
         assert e.value.status == -4
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_overflow_path_and_capacity_growth(Sim, orc, variant):
+    """All beads squeezed into a quarter of the box (density 12): tiles
+    overflow shared memory and take the global-memory path, whose set-up
+    forces must match the oracle; synchronising calls then grow the tile
+    capacity until no tile overflows, and the shared-memory path gives the
+    same forces."""
+    L, nd = 48.0, 3456
+    x, _ = synth.dimers(nd, L, 0.5, seed=21)
+    x = synth.on_grid(x * 0.5, L)
+    v = synth.velocities(2 * nd, 0.5, seed=22)
+    fo, _ = orc.forces(oparams(orc, L, seed=4), x, v.astype(np.float64), 3, cells=True)
+    with Sim(L, 2 * nd, **sim_kw(seed=4, variant=variant)) as s:
+        s.set_positions(x, v, step=3)
+        _, _, f1, _ = s.get_state()
+        ovf = s.info().overflow_tiles
+        assert ovf > 0
+        force_check(f1, fo)
+        grew = False
+        for _ in range(12):
+            s.step(1)
+            s.sync()
+            o = s.info().overflow_tiles
+            if o == ovf:
+                grew = True
+                break
+            ovf = o
+        assert grew, "capacity did not grow to fit the dense tiles"
+        s.set_positions(x, v, step=3)
+        _, _, f2, _ = s.get_state()
+        assert s.info().overflow_tiles == ovf
+    force_check(f2, fo)
 
 
 def test_full_size_forces_sampled(Sim, orc):
