@@ -39,7 +39,14 @@ CONFIGS = {
     "c2": dict(L=256.0, n_beads=3 * 256 * 256, name="c2-size: L=256, density 3, 196,608 beads"),
     "c1": dict(L=32.0, n_beads=1024, name="c1: L=32, 512 dimers"),
 }
-OPS_PER_BEAD_STEP = 650.0      # algorithmic ALU operations per bead-step
+# algorithmic ALU operations per bead-step: ~13.5 half-stencil distance tests
+# x ~8 ops + ~4.7 pairs x (Philox4x32-10 ~80 + force ~30) + bond, propulsion,
+# drag and integration
+OPS_PER_BEAD_STEP = 650.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_force<8, 0, 2> launch at
+# the 3,145,728-bead workload, one ncu capture of this build
+# (profiles/force_integrate_traffic_c3.md); None once the kernel changes
+FORCE_TRAFFIC_BYTES_C3 = 257.87e6
 BYTES_PER_BEAD_STEP = 36.0     # algorithmic HBM bytes per bead-step (read 20, write 16)
 N_SM, LANES = 152, 128
 
@@ -163,6 +170,59 @@ def ensemble_leg(R, steps, warmup, seed=0):
             "timing": "wall clock around each leg, synchronised; sequential = each replica alone, one after another"}
 
 
+def surrogate_leg(n_train=64, n_test=16, seed=0):
+    """Learned surrogate, scaled-down version of the paper-point study:
+    statistics of n_train + n_test parameter points (area fraction U(0.1, 0.6),
+    gamma log-U(1, 20), zeta log-U(0.01, 1), f_p U(0.5, 2)) from the batched
+    ensemble (L = 32, 600 steps burn-in, 4 snapshots 100 steps apart), a
+    4-member surrogate trained on the first n_train, then its held-out error,
+    fallback rate and prediction throughput (4096-row calls through the C ABI,
+    host copies included)."""
+    import numpy as np
+    from paper_1310_0998_gb300 import surrogate as S
+    rng = np.random.default_rng(seed + 17)
+    n = n_train + n_test
+    X = np.stack([rng.uniform(0.1, 0.6, n), np.exp(rng.uniform(0.0, np.log(20.0), n)),
+                  np.exp(rng.uniform(np.log(0.01), 0.0, n)), rng.uniform(0.5, 2.0, n)], axis=1)
+    t0 = time.perf_counter()
+    Y = S.simulate(X, L=32.0, burn=600, n_snap=4, every=100, seed=seed, batched=True)
+    t_sim = time.perf_counter() - t0
+    sur = S.Surrogate(members=4, max_rows=4096, seed=seed)
+    try:
+        t0 = time.perf_counter()
+        loss = sur.fit(X[:n_train], Y[:n_train], epochs=300, batch=32, lr=2e-3)
+        t_fit = time.perf_counter() - t0
+        sd = Y[:n_train].std(axis=0) + 1e-12
+        P, Sd = sur.predict(X[n_train:])
+        err = float(np.sqrt(np.mean(((P - Y[n_train:]) / sd) ** 2)))
+        Pt, St = sur.predict(X[:n_train])
+        thr = 2.0 * float(np.max(St / (np.abs(Pt) + 1.0)))
+        fb = float(np.mean(np.max(Sd / (np.abs(P) + 1.0), axis=1) > thr))
+        rows = 4096
+        Xb = np.resize(X, (rows, 4)).astype(np.float32)
+        for _ in range(3):
+            sur.predict(Xb)
+        reps = 20
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sur.predict(Xb)
+        t_pred = (time.perf_counter() - t0) / reps
+    finally:
+        sur.close()
+    flops = 2.0 * 4 * rows * (16 * 256 + 256 * 256 + 256 * 48)
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    return {"train_points": n_train, "test_points": n_test, "members": 4, "targets": 40,
+            "simulate_s": t_sim, "simulate_s_per_point": t_sim / n, "train_s": t_fit, "train_loss": loss,
+            "heldout_rms_err_in_sd": err, "fallback_rate": fb, "fallback_threshold": thr,
+            "predict_rows_per_s": rows / t_pred, "predict_s_per_point": t_pred / rows,
+            "speedup_vs_simulation_per_point": (t_sim / n) / (t_pred / rows),
+            "predict_tflops": flops / t_pred / 1e12, "tensor_peak_tflops": peak,
+            "tensor_frac": flops / t_pred / 1e12 / peak,
+            "note": "BF16 mma.sync GEMMs of 4096 x {16,256,256} x {256,256,48} per member; "
+                    "wall clock per C-ABI call including host copies"}
+
+
 def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -201,6 +261,7 @@ def main():
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue, 3 grid-order queue")
     ap.add_argument("--tile", type=int, default=0, help="cell-block side: 0 default, 4, 8, 16")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
@@ -313,7 +374,9 @@ def main():
                    "l2": "512 MiB write+read flush between timed steps",
                    "pairs_per_bead": npairs / nb, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "force_integrate", "achieved": alu_ach / 1e12,
-                     "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": None,
+                     "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": (FORCE_TRAFFIC_BYTES_C3 if cfg["name"].startswith("c3") and info.tile == 8
+                                 and info.variant == 2 else None),
+                     "traffic_unit": "bytes per launch (ncu, final step of a call)",
                      "peak_src": f"{N_SM} SMs x {LANES} lanes x {pk['sm_max_mhz']:.0f} MHz",
                      "ms": force_s * 1e3},
         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm"], "frac": hbm_ach / pk["hbm"],
@@ -328,6 +391,8 @@ def main():
     }
     if rank == 0 and not args.no_ensemble:
         line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup)
+    if rank == 0 and not args.no_surrogate:
+        line["surrogate"] = surrogate_leg()
     if rank == 0 and not args.no_cpu:
         Lc = 128.0 if nb > 200000 else L
         nbc = int(round(nb * (Lc / L) ** 2)) // 2 * 2

@@ -11,7 +11,7 @@ wrapped into [0, L).  Positions are returned as float64 values on the grid
 x = X L / 2^32 with integer X (the simulator's fixed-point state holds them
 exactly, so both sides start from the same bits); velocities are float32.
 
-Workloads (seed 0 unless stated), in BASELINE units (r_c = 1, m = 1):
+Workloads (seed 0 unless stated), in reduced units (r_c = 1, m = 1):
   C1  L=32, 512 dimers, a=25, gamma=4.5, kBT=1, kappa=100, r0=0.5, f_p=1,
       zeta=0.1, dt=0.01.
   C2  L=256, area fraction phi -> N_d = 2 phi L^2, gamma in {1, 4.5, 20},

@@ -1,6 +1,6 @@
 """GPU parity of the simulation hot path against the FP64 oracle.
 
-Tolerances (written here, from the BASELINE the benchmark spec):
+Tolerances (written here, from the hot path's stated parity bounds):
   forces at identical input state: ||F_gpu - F_orc|| / ||F_orc|| <= 1e-5 and
     max_i |dF_i| <= 1e-5 * max(|F_i|, F_rms);
   positions after 100 steps (C1): max |minimg(x_gpu - x_orc)| <= 1e-4;
