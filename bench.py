@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--wexp", type=float, default=0.0,
+                    help="exponent s of w in the dissipative/random forces (0 = 2, the printed form)")
     ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue, 3 grid-order queue")
     ap.add_argument("--tile", type=int, default=0, help="cell-block side: 0 default, 4, 8, 16")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
@@ -290,7 +292,7 @@ def main():
     x, v = synth.dimers(nb // 2, L, PHYS["r0"], seed=rank)
     sim = Sim(L, nb, stream=stream.cuda_stream, seed=rank, a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"],
               rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"],
-              dt=PHYS["dt"], mass=PHYS["mass"], variant=args.variant, tile=args.tile)
+              dt=PHYS["dt"], mass=PHYS["mass"], variant=args.variant, tile=args.tile, wexp=args.wexp)
     sim.set_positions(x, v)
     for _ in range(args.warmup):
         sim.step(1)
@@ -370,12 +372,12 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "beads": nb, "L": L, "bead_density": nb / L / L,
-                   "tile": info.tile, "variant": info.variant,
+                   "tile": info.tile, "variant": info.variant, "wexp": args.wexp if args.wexp > 0 else 2.0,
                    "l2": "512 MiB write+read flush between timed steps",
                    "pairs_per_bead": npairs / nb, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "force_integrate", "achieved": alu_ach / 1e12,
                      "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": (FORCE_TRAFFIC_BYTES_C3 if cfg["name"].startswith("c3") and info.tile == 8
-                                 and info.variant == 2 else None),
+                                 and info.variant == 2 and args.wexp in (0.0, 2.0) else None),
                      "traffic_unit": "bytes per launch (ncu, final step of a call)",
                      "peak_src": f"{N_SM} SMs x {LANES} lanes x {pk['sm_max_mhz']:.0f} MHz",
                      "ms": force_s * 1e3},

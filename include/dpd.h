@@ -82,8 +82,14 @@ typedef struct dpd_params {
     int32_t tile;          /* cell-block side in cells: 0 = default, else
                               one of 4, 8, 16                                */
     int32_t variant;       /* pair-kernel variant: 0 = default (fastest),
-                              1 = thread-per-bead, 2 = pair queue            */
+                              1 = thread-per-bead, 2 = pair queue,
+                              3 = grid-order pair queue                      */
     int32_t reserved;
+    double wexp;           /* exponent s of w in the dissipative and random
+                              forces (the changed weight exponent the closing
+                              section proposes): w_D = w^s, w_R = w^(s/2), so
+                              sigma^2 = 2 gamma kBT still sets the temperature;
+                              0 or 2 = Eq. (DPDcdr) as printed; 0 <= s <= 8  */
 } dpd_params;
 
 typedef struct dpd_ctx dpd_ctx;

@@ -45,6 +45,7 @@ class OrcParams(ctypes.Structure):
         ("exclude_bonded", ctypes.c_int32),
         ("noise", ctypes.c_int32),
         ("pad", ctypes.c_int32),
+        ("wexp", ctypes.c_double),
     ]
 
 
@@ -89,10 +90,10 @@ def lib():
 
 
 def params(L, a, gamma, kBT, rc, kbond, r0, fp, zeta, dt, mass=1.0, seed=0, replica=0,
-           exclude_bonded=1, noise=0) -> OrcParams:
+           exclude_bonded=1, noise=0, wexp=0.0) -> OrcParams:
     return OrcParams(float(L), float(a), float(gamma), float(kBT), float(rc), float(kbond),
                      float(r0), float(fp), float(zeta), float(dt), float(mass), int(seed),
-                     int(replica), int(exclude_bonded), int(noise), 0)
+                     int(replica), int(exclude_bonded), int(noise), 0, float(wexp))
 
 
 def _c(a, dtype):

@@ -65,6 +65,8 @@ typedef struct {
     int32_t exclude_bonded;  /* 1: no pair force between bonded beads      */
     int32_t noise;           /* 0: uniform alpha, 1: Gaussian alpha        */
     int32_t pad;
+    double wexp;             /* exponent s of the dissipative weight        */
+                             /* w_D = w^s, w_R = w^(s/2); 0 selects s = 2   */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -129,6 +131,10 @@ static double minimg(double d, double L)
 
 /* One DPD pair term, Eqs. (DPDf), (DPDcdr), (weightFunc01).  e = (r_i - r_j)/r,
  * so the conservative part A w e pushes i away from j (soft repulsion, Sec. 4).
+ * The dissipative and random parts carry w_D = w^s and w_R = w^(s/2): s = 2 is
+ * Eq. (DPDcdr) as printed; another s is the changed exponent of w that the
+ * closing section proposes, with w_D = w_R^2 so that sigma^2 = 2 gamma kBT
+ * still holds the temperature.
  * Returns 1 and the force on i when r < r_c and r > 0, else 0. */
 static int pair_force(const orc_params *p, double dx, double dy, double dvx, double dvy,
                       uint32_t i, uint32_t j, int64_t step, double *fx, double *fy)
@@ -141,9 +147,12 @@ static int pair_force(const orc_params *p, double dx, double dy, double dvx, dou
     double dve = dvx * ex + dvy * ey;
     double sigma = sqrt(2.0 * p->gamma * p->kBT);
     double alpha = orc_alpha(i, j, step, p->seed, p->replica, p->noise);
+    double s = p->wexp > 0.0 ? p->wexp : 2.0;
+    double wd = s == 2.0 ? w * w : pow(w, s);
+    double wr = s == 2.0 ? w : pow(w, 0.5 * s);
     double fc = p->a * w;
-    double fd = -p->gamma * w * w * dve;
-    double fr = sigma * w * alpha / sqrt(p->dt);
+    double fd = -p->gamma * wd * dve;
+    double fr = sigma * wr * alpha / sqrt(p->dt);
     double F = fc + fd + fr;
     *fx = F * ex;
     *fy = F * ey;

@@ -48,6 +48,7 @@ class DpdParams(ctypes.Structure):
         ("tile", ctypes.c_int32),
         ("variant", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("wexp", ctypes.c_double),
     ]
 
 

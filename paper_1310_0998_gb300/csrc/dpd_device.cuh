@@ -43,6 +43,8 @@ struct Sys {
     float L, ulen, inv_ulen, cs;   // ulen = L / 2^32, inv_ulen = 2^32 / L
     int nc, ntx, n, ncells;
     float rc2, inv_rc, a, gamma, sig_r, kbond, r0, fp, zeta, dt, hdtm;
+    float hwexp;                   // s/2 of w_R = w^(s/2) when gen_w
+    int gen_w;                     // 1: dissipative weight exponent s != 2
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];   // Philox round keys key + r * (Weyl increments)
     int noise, excl, cap;

@@ -193,6 +193,7 @@ int validate(const dpd_params *p)
     if (!(p->tile == 0 || p->tile == 4 || p->tile == 8 || p->tile == 16)) return DPD_ERR_INVALID_ARG;
     if (p->variant < 0 || p->variant > 3) return DPD_ERR_INVALID_ARG;
     if (p->noise < 0 || p->noise > 1) return DPD_ERR_INVALID_ARG;
+    if (!(p->wexp >= 0.0 && p->wexp <= 8.0)) return DPD_ERR_INVALID_ARG;
     const int nc = n_cells_side(p->L, p->rc);
     if (nc < 3 || (double)nc * nc >= 2.0e9) return DPD_ERR_INVALID_ARG;
     return DPD_OK;
@@ -220,6 +221,9 @@ void fill_physics(Sys &d, const dpd_params *p)
     }
     d.noise = p->noise;
     d.excl = p->exclude_bonded ? 1 : 0;
+    const double s = p->wexp > 0.0 ? p->wexp : 2.0;
+    d.gen_w = s != 2.0 ? 1 : 0;
+    d.hwexp = (float)(0.5 * s);
 }
 
 void fill_geometry(Sys &d, const dpd_params *p, int B)

@@ -233,7 +233,10 @@ __device__ __forceinline__ float dpd_pair_scalar(const Sys &d, float dx, float d
     ey = dy * rinv;
     const float dve = dvx * ex + dvy * ey;
     const float nz = pair_noise(d, idi, idj, s_lo, s_hi);
-    return w * (d.a - d.gamma * w * dve + d.sig_r * nz);
+    if (!d.gen_w) return w * (d.a - d.gamma * w * dve + d.sig_r * nz);
+    // changed exponent of w: w_R = w^(s/2), w_D = w_R^2 (uniform branch)
+    const float wr = __powf(w, d.hwexp);
+    return d.a * w - d.gamma * (wr * wr) * dve + d.sig_r * wr * nz;
 }
 
 

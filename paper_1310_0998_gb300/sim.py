@@ -9,7 +9,7 @@ from . import _lib
 from ._lib import DpdInfo, DpdParams, check, ptr, where
 
 DEFAULTS = dict(a=25.0, gamma=4.5, kBT=1.0, rc=1.0, k_bond=100.0, r0=0.5, f_p=1.0, zeta=0.1,
-                dt=0.01, mass=1.0, seed=0, replica=0, exclude_bonded=1, noise=0, tile=0, variant=0)
+                dt=0.01, mass=1.0, seed=0, replica=0, exclude_bonded=1, noise=0, tile=0, variant=0, wexp=0.0)
 
 
 def make_params(L: float, n_beads: int, **kw) -> DpdParams:
@@ -20,7 +20,8 @@ def make_params(L: float, n_beads: int, **kw) -> DpdParams:
     return DpdParams(float(L), int(n_beads), float(v["a"]), float(v["gamma"]), float(v["kBT"]),
                      float(v["rc"]), float(v["k_bond"]), float(v["r0"]), float(v["f_p"]), float(v["zeta"]),
                      float(v["dt"]), float(v["mass"]), int(v["seed"]), int(v["replica"]),
-                     int(v["exclude_bonded"]), int(v["noise"]), int(v["tile"]), int(v["variant"]), 0)
+                     int(v["exclude_bonded"]), int(v["noise"]), int(v["tile"]), int(v["variant"]), 0,
+                     float(v["wexp"]))
 
 
 class Sim:

@@ -64,6 +64,31 @@ def test_batch_matches_single_system(mods, variant):
         np.testing.assert_allclose(logs[r][:, 0], log[:, 0], rtol=1e-4)
 
 
+def test_batch_with_weight_exponents(mods):
+    """Replicas with different exponents of w in one persistent launch match
+    the same replicas run alone."""
+    Ensemble, Sim = mods
+    pts = [dict(p, wexp=s) for p, s in zip(_points()[:4], (0.0, 0.5, 3.0, 1.0))]
+    states = []
+    with Ensemble(pts) as ens:
+        for r, pt in enumerate(pts):
+            x, _ = synth.dimers(pt["n_beads"] // 2, pt["L"], 0.5, seed=40 + r)
+            v = synth.velocities(pt["n_beads"], 0.5, seed=50 + r)
+            ens.replica(r).set_positions(x, v)
+            states.append((x, v))
+        ens.step(30)
+        ens.sync()
+        got = [ens.replica(r).get_state() for r in range(len(pts))]
+    for r, pt in enumerate(pts):
+        kw = {k: v for k, v in pt.items() if k not in ("L", "n_beads")}
+        with Sim(pt["L"], pt["n_beads"], **kw) as s:
+            s.set_positions(*states[r])
+            s.step(30)
+            xs, vs, _, _ = s.get_state()
+        assert np.abs(minimg(got[r][0] - xs, pt["L"])).max() < 1e-5, r
+        np.testing.assert_allclose(got[r][1], vs, atol=1e-3)
+
+
 def test_batch_against_oracle(mods, orc):
     """One replica of the batch against the FP64 oracle, 100 steps."""
     Ensemble, _ = mods

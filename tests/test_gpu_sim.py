@@ -40,7 +40,7 @@ def sim_kw(seed=0, **kw):
     p.update(kw)
     return dict(a=p["a"], gamma=p["gamma"], kBT=p["kBT"], rc=p["rc"], k_bond=p["kbond"], r0=p["r0"],
                 f_p=p["fp"], zeta=p["zeta"], dt=p["dt"], mass=p["mass"], seed=seed,
-                **{k: v for k, v in kw.items() if k in ("tile", "noise", "exclude_bonded", "variant")})
+                **{k: v for k, v in kw.items() if k in ("tile", "noise", "exclude_bonded", "variant", "wexp")})
 
 
 def minimg(d, L):
@@ -130,6 +130,34 @@ def test_trajectory_parity_c1_100_steps(Sim, orc, variant):
     assert np.abs(vg - st.v).max() <= 2e-2
     rel = np.linalg.norm(f - st.f) / np.linalg.norm(st.f)
     assert rel <= 1e-3, rel
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("s", [0.5, 1.0, 3.0])
+def test_weight_exponent_force_parity(Sim, orc, s, variant):
+    """Changed exponent of w (w_D = w^s, w_R = w^(s/2)): set-up forces
+    against the oracle on a ragged multi-tile box."""
+    L, nd = 37.0, 600
+    x, _ = synth.dimers(nd, L, 0.5, seed=31)
+    v = synth.velocities(2 * nd, 1.0, seed=32)
+    with Sim(L, 2 * nd, **sim_kw(seed=5, variant=variant, wexp=s)) as sm:
+        sm.set_positions(x, v, step=7)
+        _, _, f, _ = sm.get_state()
+    fo, _ = orc.forces(oparams(orc, L, seed=5, wexp=s), x, v.astype(np.float64), 7)
+    force_check(f, fo)
+
+
+def test_weight_exponent_trajectory(Sim, orc):
+    """s = 0.5, C1 geometry: positions after 100 steps within 1e-4."""
+    L, nd = 32.0, 512
+    x, v = synth.dimers(nd, L, 0.5, seed=0)
+    with Sim(L, 2 * nd, **sim_kw(seed=0, wexp=0.5)) as sm:
+        sm.set_positions(x, v)
+        sm.step(100)
+        xg, _, _, _ = sm.get_state()
+    st = orc.State(oparams(orc, L, seed=0, wexp=0.5), x, v)
+    st.run(100)
+    assert np.abs(minimg(xg - st.x, L)).max() <= 1e-4
 
 
 def test_thermo_fp64_reductions(Sim):

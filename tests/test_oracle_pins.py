@@ -241,6 +241,54 @@ def test_equilibrium_temperature(orc):
     assert abs(T.mean() - 1.0) < 0.02, T.mean()
 
 
+def test_weight_exponent_reduces_to_printed_form(orc):
+    """The changed-exponent path (pow) at s = 2 + 1e-12 gives the forces of the
+    printed Eq. (DPDcdr) (w^2 and w, the s = 2 path) to rounding."""
+    L = 9.0
+    x, _ = synth.dimers(150, L, 0.5, seed=4)
+    v = synth.velocities(300, 1.0, seed=5)
+    f2, n2 = orc.forces(P(orc, L=L), x, v.astype(np.float64), 3)
+    fs, ns = orc.forces(P(orc, L=L, wexp=2.0 + 1e-12), x, v.astype(np.float64), 3)
+    assert n2 == ns
+    np.testing.assert_allclose(fs, f2, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("s", [0.5, 1.0, 3.0])
+def test_weight_exponent_power_laws(orc, s):
+    """With the exponent s, the random part scales as w^(s/2) and the
+    dissipative part as w^s with the separation (same pair, same step, so the
+    same alpha): ratios at two separations along e."""
+    v0 = np.zeros((2, 2))
+    vr = np.array([[0.0, 0.0], [0.0, 0.7]])   # j (above i) recedes along +y
+    r1, r2 = 0.35, 0.8
+    w1, w2 = 1 - r1, 1 - r2
+    out = {}
+    for r in (r1, r2):
+        x = np.array([[5.0, 5.0], [5.0, 5.0 + r]])
+        fr = orc.pair_forces_only(P(orc, a=0.0, gamma=2.0, kBT=1.0, wexp=s, exclude_bonded=0), x, v0, 9)
+        fd = orc.pair_forces_only(P(orc, a=0.0, gamma=2.0, kBT=0.0, wexp=s, exclude_bonded=0), x, vr, 9)
+        out[r] = (fr[0, 1], fd[0, 1])
+    np.testing.assert_allclose(out[r1][0] / out[r2][0], (w1 / w2) ** (s / 2), rtol=1e-12)
+    np.testing.assert_allclose(out[r1][1] / out[r2][1], (w1 / w2) ** s, rtol=1e-12)
+    # the dissipative force opposes the separation: it pulls i after j (+y)
+    assert out[r1][1] > 0 and out[r2][1] > 0
+
+
+def test_equilibrium_temperature_changed_weight_exponent(orc):
+    """s = 0.5: w_D = w_R^2 keeps the fluctuation-dissipation balance, so the
+    thermostat still holds T = kBT (zeta = f_p = 0).  Were the random weight
+    w^s instead of w^(s/2), T would settle near 0.63 kBT."""
+    L = 32.0
+    x, v = synth.dimers(512, L, 0.5, seed=0)
+    p = P(orc, L=L, zeta=0.0, fp=0.0, seed=12, dt=0.005, wexp=0.5)
+    st = orc.State(p, x, v, cells=True)
+    st.run(2000)
+    log = st.run(18000, thermo=True)
+    n = x.shape[0]
+    T = 2 * log[:, 0] / (2 * n - 2)
+    assert abs(T.mean() - 1.0) < 0.02, T.mean()
+
+
 def test_cell_list_variant_matches_all_pairs(orc):
     L = 9.0
     x, _ = synth.dimers(150, L, 0.5, seed=2)
