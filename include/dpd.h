@@ -190,6 +190,13 @@ int dpd_energy_spectrum(dpd_ctx *ctx, int M, double eps, double *E);
  * values, so serialise them.  Synchronises. */
 int dpd_energy_spectrum_noalloc(dpd_ctx *ctx, int M, double eps, double *E);
 
+/* Sec. 5.3: scalar vorticity omega = (curl u_M) . e_z of the filtered field
+ * above (same M, eps), by second-order central differences on the periodic
+ * grid: omega = (u_y[iy][ix+1] - u_y[iy][ix-1] - u_x[iy+1][ix] + u_x[iy-1][ix])
+ * M / (2 L).  omega: host [M][M] (row = y).  3 <= M <= 1024.  FP64.
+ * Synchronises. */
+int dpd_vorticity(dpd_ctx *ctx, int M, double eps, double *omega);
+
 /* Eqs. (VCF), (spatial01): all agent pairs with COM separation in
  * [b dr, (b+1) dr), b < nbins (nbins dr <= L/2 advised):
  *   g[b] = (<v_a.v_b>_b - |<v>|^2) / (<|v|^2> - |<v>|^2) (global means),

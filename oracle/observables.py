@@ -22,6 +22,8 @@ garbled):
       g(b) = (<v_a.v_b>_b - |<v>|^2) / (<|v|^2> - |<v>|^2).
   * Integral length: trapezoid over the nodes r = 0 (g = 1) and the bin
     centres (b + 1/2) dr of the non-empty bins.
+  * Vorticity omega = (curl u_M) . e_z (Sec. 5.3): second-order central
+    differences on the periodic grid of u_M.
 """
 from __future__ import annotations
 
@@ -72,6 +74,17 @@ def velocity_field(c, vc, L, M, eps, chunk=65536):
     u[..., 0][nz] = sx[nz] / n[nz]
     u[..., 1][nz] = sy[nz] / n[nz]
     return u, n
+
+
+def vorticity(u, L):
+    """Scalar vorticity omega = (curl u_M) . e_z of a field u [iy, ix, comp]
+    on the periodic M x M grid of spacing L / M (Sec. 5.3): second-order
+    central differences, omega = d u_y / dx - d u_x / dy."""
+    u = np.asarray(u, np.float64)
+    h = L / u.shape[0]
+    duy_dx = (np.roll(u[..., 1], -1, axis=1) - np.roll(u[..., 1], 1, axis=1)) / (2.0 * h)
+    dux_dy = (np.roll(u[..., 0], -1, axis=0) - np.roll(u[..., 0], 1, axis=0)) / (2.0 * h)
+    return duy_dx - dux_dy
 
 
 def fourier(u):

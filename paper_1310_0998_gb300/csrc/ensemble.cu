@@ -7,8 +7,9 @@
 // descriptors, two work lists and one kernel that runs n whole steps for all
 // replicas: per step three phases (cell scan, scatter, fused force/integrate)
 // separated by grid-wide barriers.  Block b takes work items b, b + G,
-// b + 2G, ... (G blocks) of each phase's list (a replica to scan, a
-// 1024-bead chunk to scatter, a (replica, cell block) to integrate); the host
+// b + 2G, ... (G blocks) of each phase's list (a 4096-cell chunk of a
+// replica's decoupled look-back scan, a 1024-bead chunk to scatter, a
+// (replica, cell block) to integrate); the host
 // shuffles the lists once with a fixed seed so that uneven replicas spread
 // evenly over the blocks.  (Items handed out by atomic counters that block 0
 // reset between phases were measured to process some cell blocks twice; the
@@ -29,67 +30,6 @@
 namespace dpd {
 
 constexpr int ENS_CHUNK = 1024;   // beads per scatter work item
-
-// Exclusive scan of one system's cell counts by a single block, chunk by
-// chunk with a running carry (replica boxes hold at most a few 10^4 cells);
-// also advances the replica's step and clears its thermo slot.
-__device__ void scan_block(const Sys &d)
-{
-    __shared__ uint32_t s_w[TILE_THREADS / 32];
-    __shared__ uint32_t s_carry, s_tot;
-    constexpr int IPT = 8;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < d.ncells; base += blockDim.x * IPT) {
-        uint32_t v[IPT], sum = 0;
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            const int idx = base + tid * IPT + k;
-            v[k] = idx < d.ncells ? d.counts[idx] : 0u;
-            sum += v[k];
-            if (idx < d.ncells) d.counts[idx] = 0u;
-        }
-        uint32_t incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_w[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            const uint32_t w = lane < nw ? s_w[lane] : 0u;
-            uint32_t wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += t;
-            }
-            if (lane < nw) s_w[lane] = wi - w;
-            if (lane == nw - 1) s_tot = wi;
-        }
-        __syncthreads();
-        uint32_t run = s_carry + s_w[wid] + (incl - sum);
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            const int idx = base + tid * IPT + k;
-            if (idx < d.ncells) d.cstart[idx] = run;
-            run += v[k];
-        }
-        __syncthreads();
-        if (tid == 0) s_carry += s_tot;
-        __syncthreads();
-    }
-    if (tid == 0) {
-        d.cstart[d.ncells] = s_carry;
-        const long long s1 = *d.step + 1;
-        *d.step = s1;
-        double *th = d.thermo + 4 * (size_t)(s1 % THERMO_CAP);
-        th[0] = 0.0; th[1] = 0.0; th[2] = 0.0; th[3] = 0.0;
-    }
-    __syncthreads();
-}
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
@@ -126,16 +66,21 @@ __device__ void grid_barrier(unsigned *bar, unsigned nblocks, int *err, int skip
 }
 
 template <int B, int VAR>
-__global__ void __launch_bounds__(TILE_THREADS, 6)
-    k_ensemble(const Sys *__restrict__ sys, const uint32_t *__restrict__ scan_items, int R,
+__global__ void __launch_bounds__(TILE_THREADS, 8)
+    k_ensemble(const Sys *__restrict__ sys, const uint32_t *__restrict__ scan_items, int n_scan,
                const uint32_t *__restrict__ scat, int n_scat, const uint32_t *__restrict__ tiles, int n_tiles,
                unsigned *bar, int *berr, int nsteps, int final_last)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const unsigned nb = gridDim.x;
     for (int s = 0; s < nsteps; ++s) {
-        // phase 1: cell scans, one replica per block at a time
-        for (int it = blockIdx.x; it < R; it += nb) scan_block(sys[scan_items[it]]);
+        // phase 1: cell scans; a replica of n cells contributes
+        // ceil(n / SCAN_TILE) items, each one chunk of its decoupled
+        // look-back scan (the chunk comes from the replica's ticket)
+        for (int it = blockIdx.x; it < n_scan; it += nb) {
+            const Sys &d = sys[scan_items[it]];
+            scan_decoupled_t<TILE_THREADS>(d, (d.ncells + SCAN_TILE - 1) / SCAN_TILE);
+        }
         grid_barrier(bar, nb, berr, 0);
         // phase 2: scatter U -> S in chunks of ENS_CHUNK beads
         for (int it = blockIdx.x; it < n_scat; it += nb) {
@@ -181,7 +126,7 @@ struct dpd_batch {
     uint32_t *d_scan = nullptr, *d_scat = nullptr, *d_tiles = nullptr;
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
-    int n_scat = 0, n_tiles = 0, B = 8, var = 2, cap = 0, grid = 0;
+    int n_scan = 0, n_scat = 0, n_tiles = 0, B = 8, var = 2, cap = 0, grid = 0;
     size_t smem = 0;
     cudaGraphExec_t g = nullptr;
     int64_t g_steps = -1;
@@ -215,7 +160,7 @@ static int ens_prepare(dpd_batch *b)
 template <int B, int VAR>
 static void ens_launch(dpd_batch *b, int nsteps, int final_last)
 {
-    k_ensemble<B, VAR><<<b->grid, TILE_THREADS, b->smem, b->st>>>(b->d_sys, b->d_scan, b->R, b->d_scat, b->n_scat,
+    k_ensemble<B, VAR><<<b->grid, TILE_THREADS, b->smem, b->st>>>(b->d_sys, b->d_scan, b->n_scan, b->d_scat, b->n_scat,
                                                                   b->d_tiles, b->n_tiles, b->d_bar, b->d_err, nsteps,
                                                                   final_last);
 }
@@ -247,7 +192,7 @@ static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last)
 static int ens_build_tables(dpd_batch *b)
 {
     std::vector<Sys> sys(b->R);
-    std::vector<uint32_t> scan(b->R), scat, tiles;
+    std::vector<uint32_t> order(b->R), scan, scat, tiles;
     int cap = 0;
     for (int r = 0; r < b->R; ++r) {
         sys[r] = b->reps[r]->d;
@@ -266,27 +211,30 @@ static int ens_build_tables(dpd_batch *b)
     };
     shuffle(scat);
     shuffle(tiles);
-    for (int r = 0; r < b->R; ++r) scan[r] = (uint32_t)r;
-    std::stable_sort(scan.begin(), scan.end(), [&sys](uint32_t a, uint32_t c) { return sys[a].ncells > sys[c].ncells; });
+    for (int r = 0; r < b->R; ++r) order[r] = (uint32_t)r;
+    std::stable_sort(order.begin(), order.end(), [&sys](uint32_t a, uint32_t c) { return sys[a].ncells > sys[c].ncells; });
+    for (uint32_t r : order)
+        for (int k = 0; k < (sys[r].ncells + SCAN_TILE - 1) / SCAN_TILE; ++k) scan.push_back(r);
     // every replica's tile plan fits the common shared-memory size
     for (int r = 0; r < b->R; ++r) sys[r].cap = cap;
     for (int r = 0; r < b->R; ++r) b->reps[r]->d.cap = cap;
     b->cap = cap;
     b->smem = force_smem(b->B, b->var, cap, false);
+    b->n_scan = (int)scan.size();
     b->n_scat = (int)scat.size();
     b->n_tiles = (int)tiles.size();
     if (b->pool) cudaFree(b->pool);
-    const size_t bytes = sizeof(Sys) * (size_t)b->R + 4 * (size_t)b->R + 4 * scat.size() + 4 * tiles.size() + 256 * 5;
+    const size_t bytes = sizeof(Sys) * (size_t)b->R + 4 * scan.size() + 4 * scat.size() + 4 * tiles.size() + 256 * 5;
     CUB(cudaMalloc(&b->pool, bytes));
     char *p = (char *)b->pool;
     b->d_sys = (Sys *)p; p += (sizeof(Sys) * (size_t)b->R + 255) & ~size_t(255);
-    b->d_scan = (uint32_t *)p; p += (4 * (size_t)b->R + 255) & ~size_t(255);
+    b->d_scan = (uint32_t *)p; p += (4 * scan.size() + 255) & ~size_t(255);
     b->d_scat = (uint32_t *)p; p += (4 * scat.size() + 255) & ~size_t(255);
     b->d_tiles = (uint32_t *)p; p += (4 * tiles.size() + 255) & ~size_t(255);
     b->d_bar = (unsigned *)p;          // 2 words
     b->d_err = (int *)(b->d_bar + 8);  // 1 word
     CUB(cudaMemcpyAsync(b->d_sys, sys.data(), sizeof(Sys) * (size_t)b->R, cudaMemcpyHostToDevice, b->st));
-    CUB(cudaMemcpyAsync(b->d_scan, scan.data(), 4 * (size_t)b->R, cudaMemcpyHostToDevice, b->st));
+    CUB(cudaMemcpyAsync(b->d_scan, scan.data(), 4 * scan.size(), cudaMemcpyHostToDevice, b->st));
     CUB(cudaMemcpyAsync(b->d_scat, scat.data(), 4 * scat.size(), cudaMemcpyHostToDevice, b->st));
     CUB(cudaMemcpyAsync(b->d_tiles, tiles.data(), 4 * tiles.size(), cudaMemcpyHostToDevice, b->st));
     CUB(cudaMemsetAsync(b->d_bar, 0, 64, b->st));

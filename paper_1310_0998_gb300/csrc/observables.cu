@@ -97,6 +97,20 @@ __global__ void k_field_finish(const double *sx, const double *sy, const double 
     z[g] = n > 0.0 ? make_double2(sx[g] / n, sy[g] / n) : make_double2(0.0, 0.0);
 }
 
+// Scalar vorticity of the field, omega = du_y/dx - du_x/dy (Sec. 5.3), by
+// second-order central differences on the periodic grid of spacing h.
+__global__ void k_vorticity(const double2 *__restrict__ z, int M, double inv2h, double *__restrict__ om)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M * M) return;
+    const int iy = g / M, ix = g - iy * M;
+    const int xp = ix + 1 == M ? 0 : ix + 1, xm = ix == 0 ? M - 1 : ix - 1;
+    const int yp = iy + 1 == M ? 0 : iy + 1, ym = iy == 0 ? M - 1 : iy - 1;
+    const double duy = __dsub_rn(z[(size_t)iy * M + xp].y, z[(size_t)iy * M + xm].y);
+    const double dux = __dsub_rn(z[(size_t)yp * M + ix].x, z[(size_t)ym * M + ix].x);
+    om[g] = __dsub_rn(__dmul_rn(duy, inv2h), __dmul_rn(dux, inv2h));
+}
+
 // In-place radix-2 FFT (forward, e^{-2 pi i k n / M}) of M complex doubles
 // with stride `stride` between elements and `pitch` between transforms; one
 // block per transform, M/2 threads, data staged in shared memory.
@@ -256,21 +270,24 @@ void dpd_internal_free_obs(dpd_ctx *c)
             return e_ == cudaErrorMemoryAllocation ? DPD_ERR_OOM : DPD_ERR_CUDA; \
     } while (0)
 
-// Field on the device: z [M*M] double2 (u_x, u_y), cnt [M*M].
-static int field_device(dpd_ctx *c, int M, double eps, double2 **z_out, double **cnt_out, char **tail)
+// Field on the device: z [M*M] double2 (u_x, u_y), cnt [M*M], and a tail of
+// at least tail_bytes for the caller.  Every sub-buffer starts on a 256-byte
+// boundary (z is read as double2, which needs 16; an odd M*M must not shift it).
+static int field_device(dpd_ctx *c, int M, double eps, size_t tail_bytes, double2 **z_out, double **cnt_out,
+                        char **tail)
 {
     const int na = c->d.n / 2;
     const size_t MM = (size_t)M * M;
-    const size_t bytes = 16 * (size_t)na * 2 + 8 * MM * 3 + 16 * MM + 8 * 8 + 8 * 65536 * 2 + 1024;
-    ObsScratch *s = scratch_of(c, bytes);
+    auto up = [](size_t o) { return (o + 255) & ~size_t(255); };
+    const size_t o_cc = 0, o_vv = up(o_cc + 16 * (size_t)na), o_s = up(o_vv + 16 * (size_t)na);
+    const size_t o_z = up(o_s + 24 * MM), o_tail = up(o_z + 16 * MM);
+    ObsScratch *s = scratch_of(c, o_tail + tail_bytes + 256);
     if (!s) return DPD_ERR_OOM;
     char *b = (char *)s->buf;
-    double2 *cc = (double2 *)b; b += 16 * (size_t)na;
-    double2 *vv = (double2 *)b; b += 16 * (size_t)na;
-    double *sx = (double *)b; b += 8 * MM;
-    double *sy = (double *)b; b += 8 * MM;
-    double *cn = (double *)b; b += 8 * MM;
-    double2 *z = (double2 *)b; b += 16 * MM;
+    double2 *cc = (double2 *)(b + o_cc);
+    double2 *vv = (double2 *)(b + o_vv);
+    double *sx = (double *)(b + o_s), *sy = sx + MM, *cn = sy + MM;   // contiguous: one clear
+    double2 *z = (double2 *)(b + o_z);
     const double L = c->p.L;
     if (eps <= 0.0) eps = L * std::sqrt(10.0 / (double)na);
     CUO(cudaMemsetAsync(sx, 0, 8 * MM * 3, c->st));
@@ -280,7 +297,7 @@ static int field_device(dpd_ctx *c, int M, double eps, double2 **z_out, double *
     CUO(cudaGetLastError());
     *z_out = z;
     *cnt_out = cn;
-    if (tail) *tail = b;
+    if (tail) *tail = b + o_tail;
     return DPD_OK;
 }
 
@@ -294,7 +311,7 @@ int dpd_velocity_field(dpd_ctx *c, int M, double eps, double *u, double *n_in)
     if (eps / (c->p.L / M) > 56.0) return DPD_ERR_INVALID_ARG;   // window wider than 56 grid points
     double2 *z;
     double *cn;
-    int rc = field_device(c, M, eps, &z, &cn, nullptr);
+    int rc = field_device(c, M, eps, 0, &z, &cn, nullptr);
     if (rc) return rc;
     const size_t MM = (size_t)M * M;
     CUO(cudaMemcpyAsync(u, z, 16 * MM, cudaMemcpyDeviceToHost, c->st));
@@ -311,7 +328,7 @@ int dpd_energy_spectrum(dpd_ctx *c, int M, double eps, double *E)
     double2 *z;
     double *cn;
     char *tail;
-    int rc = field_device(c, M, eps, &z, &cn, &tail);
+    int rc = field_device(c, M, eps, 8 * (size_t)(M / 2), &z, &cn, &tail);
     if (rc) return rc;
     int logM = 0;
     while ((1 << logM) < M) ++logM;
@@ -325,6 +342,26 @@ int dpd_energy_spectrum(dpd_ctx *c, int M, double eps, double *E)
     k_shells<<<(M * M + 255) / 256, 256, 0, c->st>>>(z, M, 0.5 / (M2 * M2), dE);
     CUO(cudaGetLastError());
     CUO(cudaMemcpyAsync(E, dE, 8 * (size_t)(M / 2), cudaMemcpyDeviceToHost, c->st));
+    return dpd_internal_latched(c);
+}
+
+int dpd_vorticity(dpd_ctx *c, int M, double eps, double *omega)
+{
+    if (!c || !omega || M < 3 || M > 1024) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    const int na = c->d.n / 2;
+    if (eps <= 0.0) eps = c->p.L * std::sqrt(10.0 / (double)na);
+    if (eps / (c->p.L / M) > 56.0) return DPD_ERR_INVALID_ARG;
+    const size_t MM = (size_t)M * M;
+    double2 *z;
+    double *cn;
+    char *tail;
+    int rc = field_device(c, M, eps, 8 * MM, &z, &cn, &tail);
+    if (rc) return rc;
+    double *om = (double *)tail;
+    k_vorticity<<<(int)((MM + 255) / 256), 256, 0, c->st>>>(z, M, (double)M / (2.0 * c->p.L), om);
+    CUO(cudaGetLastError());
+    CUO(cudaMemcpyAsync(omega, om, 8 * MM, cudaMemcpyDeviceToHost, c->st));
     return dpd_internal_latched(c);
 }
 

@@ -20,10 +20,16 @@ namespace dpd {
 // SCAN_TILE cells.  Logical block ids come from a monotonically growing
 // ticket so predecessors always run first; the epoch (ticket / nblocks) tags
 // the status words so nothing needs clearing between launches.  Waits are
-// bounded: on timeout the error bit is set and the scan continues.
-__device__ inline void scan_decoupled(const Sys &d, int nblocks)
+// bounded: on timeout the error bit is set and the scan continues.  NT
+// threads per block, SCAN_TILE / NT cells each: every block size cuts the
+// cells into the same SCAN_TILE chunks, so the ticket epochs of a context
+// stay consistent whichever kernel scans it.
+template <int NT>
+__device__ inline void scan_decoupled_t(const Sys &d, int nblocks)
 {
-    __shared__ uint32_t s_warp[SCAN_NT / 32];
+    constexpr int SCAN_IPT = SCAN_TILE / NT;
+    static_assert(SCAN_IPT * NT == SCAN_TILE && NT % 32 == 0 && NT <= 1024, "scan block shape");
+    __shared__ uint32_t s_warp[NT / 32];
     __shared__ uint32_t s_excl;
     __shared__ int s_bid;
     __shared__ uint32_t s_epoch;
@@ -37,18 +43,24 @@ __device__ inline void scan_decoupled(const Sys &d, int nblocks)
     const int bid = s_bid;
     const unsigned long long ep = s_epoch;
     const int base = bid * SCAN_TILE + tid * SCAN_IPT;
-    uint32_t v[SCAN_IPT];
+    // up to 16 counts per thread stay in registers; more (narrow blocks, as in
+    // the persistent ensemble kernel) are read again from L2 after the scan
+    constexpr bool KEEP = SCAN_IPT <= 16;
+    uint32_t v[KEEP ? SCAN_IPT : 1];
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_IPT; ++k) {
         const int idx = base + k;
-        v[k] = idx < d.ncells ? d.counts[idx] : 0u;
-        sum += v[k];
+        const uint32_t c = idx < d.ncells ? d.counts[idx] : 0u;
+        if constexpr (KEEP) v[k] = c;
+        sum += c;
     }
+    if constexpr (KEEP) {
 #pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        const int idx = base + k;
-        if (idx < d.ncells) d.counts[idx] = 0u;
+        for (int k = 0; k < SCAN_IPT; ++k) {
+            const int idx = base + k;
+            if (idx < d.ncells) d.counts[idx] = 0u;
+        }
     }
     // block exclusive scan of the per-thread sums
     const int lane = tid & 31, wid = tid >> 5;
@@ -61,15 +73,15 @@ __device__ inline void scan_decoupled(const Sys &d, int nblocks)
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        uint32_t w = lane < SCAN_NT / 32 ? s_warp[lane] : 0u;
+        uint32_t w = lane < NT / 32 ? s_warp[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += t;
         }
-        if (lane < SCAN_NT / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
-        if (lane == SCAN_NT / 32 - 1) {
+        if (lane < NT / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+        if (lane == NT / 32 - 1) {
             const uint32_t total = wi;
             uint32_t excl = 0;
             unsigned long long *st = d.scan_status;
@@ -102,8 +114,15 @@ __device__ inline void scan_decoupled(const Sys &d, int nblocks)
 #pragma unroll
     for (int k = 0; k < SCAN_IPT; ++k) {
         const int idx = base + k;
-        if (idx < d.ncells) d.cstart[idx] = run;
-        run += v[k];
+        if constexpr (KEEP) {
+            if (idx < d.ncells) d.cstart[idx] = run;
+            run += v[k];
+        } else if (idx < d.ncells) {
+            const uint32_t c = d.counts[idx];
+            d.counts[idx] = 0u;
+            d.cstart[idx] = run;
+            run += c;
+        }
     }
     if (bid == 0 && tid == 0) {
         const long long s1 = *d.step + 1;
@@ -112,6 +131,8 @@ __device__ inline void scan_decoupled(const Sys &d, int nblocks)
         th[0] = 0.0; th[1] = 0.0; th[2] = 0.0; th[3] = 0.0;
     }
 }
+
+__device__ inline void scan_decoupled(const Sys &d, int nblocks) { scan_decoupled_t<SCAN_NT>(d, nblocks); }
 
 // --------------------------------------------------------------- scatter ----
 template <int B>

@@ -115,6 +115,11 @@ class Sim:
         check(self._lib.dpd_energy_spectrum(self._h, int(M), float(eps), ptr(E)), "dpd_energy_spectrum")
         return E
 
+    def vorticity(self, M: int = 128, eps: float = 0.0):
+        om = np.zeros((M, M), np.float64)
+        check(self._lib.dpd_vorticity(self._h, int(M), float(eps), ptr(om)), "dpd_vorticity")
+        return om
+
     def velocity_correlation(self, dr: float, nbins: int):
         g = np.zeros(nbins, np.float64)
         num = np.zeros(nbins, np.float64)

@@ -1,0 +1,134 @@
+"""Paper-preset study (Secs. 4-5): the representative parameters of the
+numerical study, run in the batched ensemble, with the normalised energy
+spectrum, its low- and high-wavenumber slopes, the spectral peak, the
+temperature and vorticity statistics of each point.
+
+Nondimensional preset (Sec. 4, with l0 = f0 = gamma0 = 1 and m = 1):
+Phi = A = 1.5, Pe = 20 so kBT = 1/Pe = 0.05, kappa = 1000, r_c = 0.5,
+f_SP = 1 per bead, dt = 3e-3, L = 100; the bead-centre rest length is
+l - 2 r_h = 0.75 with l = 1 and aspect ratio l / 2r_h = 4; Gamma = gamma and
+Gamma_s = zeta; N = phi L^2 / (l 2 r_h) agents (4,000 at phi = 0.1,
+32,000 at phi = 0.8).  Statistics average snapshots taken every `every` steps
+after `burn` steps (the paper: every 2e4 steps within steps 1.8e6-2e6).
+
+Qualitative statements of Sec. 5.4 that the output is checked against:
+with Stokes friction the low-wavenumber slope of E/E_1 (k = 1..10) is
+positive (about 0.8) and E peaks at intermediate k (about 20); without Stokes
+friction and Gamma = 8 the low-wavenumber slope is negative.
+
+Usage: python -m paper_1310_0998_gb300.study [--burn N] [--snaps N] [--every N]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+PRESET = dict(a=1.5, kBT=0.05, rc=0.5, k_bond=1000.0, r0=0.75, f_p=1.0, dt=3.0e-3, mass=1.0)
+L_PAPER = 100.0
+
+# (phi, Gamma, Gamma_s): Stokes-friction cases and pairwise-friction-only cases
+POINTS = [(0.4, 4.0, 0.5), (0.4, 0.0, 0.5), (0.4, 4.0, 0.1), (0.4, 8.0, 0.0), (0.8, 8.0, 0.0), (0.2, 1.0, 0.0)]
+
+
+def n_agents(phi: float, L: float = L_PAPER, l: float = 1.0, r_h: float = 0.125) -> int:
+    return int(round(phi * L * L / (l * 2.0 * r_h)))
+
+
+def point(phi: float, Gamma: float, Gamma_s: float, seed: int, replica: int, L: float = L_PAPER) -> dict:
+    return dict(PRESET, L=float(L), n_beads=2 * n_agents(phi, L), gamma=float(Gamma), zeta=float(Gamma_s),
+                seed=int(seed), replica=int(replica))
+
+
+def slope(E, k0: int, k1: int) -> float:
+    """Least-squares slope of ln(E/E_1) on ln k over shells k0..k1."""
+    k = np.arange(k0, k1 + 1, dtype=np.float64)
+    y = np.log(np.asarray(E[k0 - 1:k1], np.float64) / E[0])
+    A = np.stack([np.log(k), np.ones_like(k)], axis=1)
+    return float(np.linalg.lstsq(A, y, rcond=None)[0][0])
+
+
+CHUNK = 10_000   # steps per persistent launch (a few seconds each at paper size)
+
+
+def _advance(ens, n: int):
+    while n > 0:
+        k = min(CHUNK, n)
+        ens.step(k)
+        ens.sync()
+        n -= k
+
+
+def run(points=POINTS, burn: int = 1_000_000, n_snap: int = 10, every: int = 20_000, M: int = 128,
+        seed: int = 0, L: float = L_PAPER):
+    from .ensemble import Ensemble
+    pts = [point(p, g, gs, seed + r, r, L) for r, (p, g, gs) in enumerate(points)]
+    beads = sum(p["n_beads"] for p in pts)
+    ens = Ensemble(pts)
+    E = [np.zeros(M // 2) for _ in pts]
+    T = [[] for _ in pts]
+    om_rms = [[] for _ in pts]
+    om_max = [[] for _ in pts]
+    try:
+        ens.init_random(seed)
+        t0 = time.perf_counter()
+        _advance(ens, burn)
+        t_burn = time.perf_counter() - t0
+        for _ in range(n_snap):
+            _advance(ens, every)
+            for r in range(len(pts)):
+                s = ens.replica(r)
+                E[r] += s.energy_spectrum(M) / n_snap
+                T[r].append(s.temperature())
+                om = s.vorticity(M)
+                om_rms[r].append(float(np.sqrt(np.mean(om * om))))
+                om_max[r].append(float(np.abs(om).max()))
+        t_all = time.perf_counter() - t0
+    finally:
+        ens.close()
+    out = []
+    for r, (phi, g, gs) in enumerate(points):
+        e = E[r]
+        out.append({"phi": phi, "Gamma": g, "Gamma_s": gs, "agents": pts[r]["n_beads"] // 2,
+                    "alpha_low_k1_10": slope(e, 1, 10), "alpha_high_k30_60": slope(e, 30, 60),
+                    "k_peak": int(np.argmax(e) + 1), "T": float(np.mean(T[r])),
+                    "omega_rms": float(np.mean(om_rms[r])), "omega_max": float(np.max(om_max[r])),
+                    "E_over_E1": [float(x) for x in e / e[0]]})
+    steps = burn + n_snap * every
+    return {"points": out, "beads": beads, "steps": steps, "burn": burn, "snapshots": n_snap, "every": every,
+            "wall_s": t_all, "particle_steps_per_s": beads * steps / t_all, "burn_wall_s": t_burn}
+
+
+def checks(res) -> dict:
+    """The qualitative statements of Sec. 5.4 evaluated on a run."""
+    pts = res["points"]
+    stokes = [p for p in pts if p["Gamma_s"] > 0]
+    pair_only_8 = [p for p in pts if p["Gamma_s"] == 0 and p["Gamma"] == 8.0]
+    return {
+        "stokes_low_k_slope_positive": all(p["alpha_low_k1_10"] > 0 for p in stokes),
+        "stokes_peak_at_intermediate_k": all(5 <= p["k_peak"] <= 40 for p in stokes),
+        "stokes_high_k_falls_steeply": all(p["alpha_high_k30_60"] < -1.0 for p in stokes),
+        "gamma8_no_stokes_low_k_slope_negative": all(p["alpha_low_k1_10"] < 0 for p in pair_only_8),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--burn", type=int, default=1_000_000)
+    ap.add_argument("--snaps", type=int, default=10)
+    ap.add_argument("--every", type=int, default=20_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--full", action="store_true", help="print the normalised spectra too")
+    args = ap.parse_args()
+    res = run(burn=args.burn, n_snap=args.snaps, every=args.every, seed=args.seed)
+    res["checks"] = checks(res)
+    if not args.full:
+        for p in res["points"]:
+            p.pop("E_over_E1")
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

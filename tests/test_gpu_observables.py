@@ -87,3 +87,19 @@ def test_spectrum_full_size(Sim):
     np.testing.assert_array_equal(n, no)
     np.testing.assert_allclose(u, uo, rtol=1e-10, atol=1e-12)
     np.testing.assert_allclose(E, ob.energy_spectrum(uo), rtol=1e-9)
+
+
+@pytest.mark.parametrize("L,nd,M,eps", [(32.0, 512, 128, 0.0), (37.0, 700, 63, 0.0), (64.0, 3000, 128, 3.0)])
+def test_vorticity(Sim, L, nd, M, eps):
+    """Sec. 5.3 vorticity of the filtered field against the oracle's central
+    differences of the oracle's field (odd M included)."""
+    x, v = _state(L, nd, 4, 1.0, 0.5)
+    with Sim(L, 2 * nd) as s:
+        s.set_positions(x, v)
+        om = s.vorticity(M, eps)
+    c, vc = ob.agent_com(x, v, L)
+    e = eps if eps > 0 else ob.filter_width(L, nd, 10.0)
+    uo, _ = ob.velocity_field(c, vc, L, M, e)
+    oo = ob.vorticity(uo, L)
+    np.testing.assert_allclose(om, oo, rtol=1e-9, atol=1e-10 * np.abs(oo).max())
+    assert abs(om.sum()) < 1e-9 * np.abs(om).sum()

@@ -155,3 +155,53 @@ def test_trapezoid_closed_form():
     Lg = ob.integral_length(g, cnt, dr)
     rl = r[-1]
     np.testing.assert_allclose(Lg, rl - rl ** 2 / (2 * R), rtol=1e-12)
+
+
+def _grid(M, L):
+    g = (np.arange(M) + 0.5) * (L / M)
+    X, Y = np.meshgrid(g, g, indexing="xy")   # [iy, ix]
+    return X, Y
+
+
+@pytest.mark.parametrize("m", [1, 3, 7])
+def test_vorticity_of_a_shear_wave(m):
+    """u = (sin(k y), 0), k = 2 pi m / L: the central difference of a sine is
+    the exact discrete form, omega = -(sin(k h) / h) cos(k y)."""
+    M, L = 64, 40.0
+    h = L / M
+    X, Y = _grid(M, L)
+    k = 2 * math.pi * m / L
+    u = np.zeros((M, M, 2))
+    u[..., 0] = np.sin(k * Y)
+    om = ob.vorticity(u, L)
+    np.testing.assert_allclose(om, -(math.sin(k * h) / h) * np.cos(k * Y), atol=1e-12)
+
+
+def test_vorticity_of_a_discrete_gradient_vanishes():
+    """u = (D_x phi, D_y phi) with the same central differences: the discrete
+    curl of a discrete gradient is zero (the difference operators commute)."""
+    M, L = 48, 30.0
+    h = L / M
+    rng = np.random.default_rng(2)
+    phi = rng.standard_normal((M, M))
+    u = np.zeros((M, M, 2))
+    u[..., 0] = (np.roll(phi, -1, axis=1) - np.roll(phi, 1, axis=1)) / (2 * h)
+    u[..., 1] = (np.roll(phi, -1, axis=0) - np.roll(phi, 1, axis=0)) / (2 * h)
+    assert np.abs(ob.vorticity(u, L)).max() < 1e-12
+
+
+def test_vorticity_sign_and_zero_mean():
+    """A counter-clockwise cell (u = (-sin(k y), sin(k x))) has omega > 0 at
+    its centre; on a periodic grid the vorticity of any field sums to zero."""
+    M, L = 32, 16.0
+    X, Y = _grid(M, L)
+    k = 2 * math.pi / L
+    u = np.zeros((M, M, 2))
+    u[..., 0] = -np.sin(k * (Y - L / 4))
+    u[..., 1] = np.sin(k * (X - L / 4))
+    om = ob.vorticity(u, L)
+    iy = ix = int(round(L / 4 / (L / M) - 0.5))
+    assert om[iy, ix] > 0
+    rng = np.random.default_rng(3)
+    w = ob.vorticity(rng.standard_normal((M, M, 2)), L)
+    assert abs(w.sum()) < 1e-10 * np.abs(w).sum()
