@@ -13,8 +13,10 @@ after `burn` steps (the paper: every 2e4 steps within steps 1.8e6-2e6).
 
 Qualitative statements of Sec. 5.4 that the output is checked against:
 with Stokes friction the low-wavenumber slope of E/E_1 (k = 1..10) is
-positive (about 0.8) and E peaks at intermediate k (about 20); without Stokes
-friction and Gamma = 8 the low-wavenumber slope is negative.
+positive (about 0.8), E peaks at intermediate k (about 20) and falls steeply
+beyond the peak (about k^-4; fitted here over k = 20..40, between the peak and
+the injection band near k = 50 that the paper marks); without Stokes friction
+and Gamma = 8 the low-wavenumber slope is negative.
 
 Usage: python -m paper_1310_0998_gb300.study [--burn N] [--snaps N] [--every N]
 """
@@ -92,7 +94,7 @@ def run(points=POINTS, burn: int = 1_000_000, n_snap: int = 10, every: int = 20_
     for r, (phi, g, gs) in enumerate(points):
         e = E[r]
         out.append({"phi": phi, "Gamma": g, "Gamma_s": gs, "agents": pts[r]["n_beads"] // 2,
-                    "alpha_low_k1_10": slope(e, 1, 10), "alpha_high_k30_60": slope(e, 30, 60),
+                    "alpha_low_k1_10": slope(e, 1, 10), "alpha_high_k20_40": slope(e, 20, 40),
                     "k_peak": int(np.argmax(e) + 1), "T": float(np.mean(T[r])),
                     "omega_rms": float(np.mean(om_rms[r])), "omega_max": float(np.max(om_max[r])),
                     "E_over_E1": [float(x) for x in e / e[0]]})
@@ -109,7 +111,7 @@ def checks(res) -> dict:
     return {
         "stokes_low_k_slope_positive": all(p["alpha_low_k1_10"] > 0 for p in stokes),
         "stokes_peak_at_intermediate_k": all(5 <= p["k_peak"] <= 40 for p in stokes),
-        "stokes_high_k_falls_steeply": all(p["alpha_high_k30_60"] < -1.0 for p in stokes),
+        "stokes_high_k_falls_steeply": all(p["alpha_high_k20_40"] < -2.0 for p in stokes),
         "gamma8_no_stokes_low_k_slope_negative": all(p["alpha_low_k1_10"] < 0 for p in pair_only_8),
     }
 
