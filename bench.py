@@ -34,6 +34,24 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PHYS = dict(a=25.0, gamma=4.5, kBT=1.0, rc=1.0, kbond=100.0, r0=0.5, fp=1.0, zeta=0.1, dt=0.01, mass=1.0)
+
+
+def max_over_ranks(t_local: float, world: int, device="cpu") -> float:
+    """The slowest rank's timed-region duration (every rank runs the same
+    amount of work); a no-op on one rank."""
+    if world <= 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, steps: int, t_max: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest time
+    (replicas only: each rank advances its own box of units_per_rank beads)."""
+    return world * units_per_rank * steps / t_max
 CONFIGS = {
     "c3": dict(L=1024.0, n_beads=3 * 1024 * 1024, name="c3: L=1024, density 3, 3,145,728 beads"),
     "c2": dict(L=256.0, n_beads=3 * 256 * 256, name="c2-size: L=256, density 3, 196,608 beads"),
@@ -329,13 +347,10 @@ def main():
     clk = clocks.stop()
     sim.sync()
     step_ms = np.array([a.elapsed_time(b) for a, b in evs])
-    t_dev = float(step_ms.sum()) / 1e3
+    t_dev = max_over_ranks(float(step_ms.sum()) / 1e3, world, dev)
     if world > 1:
-        t = torch.tensor([t_dev], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
         dist.barrier()
-    value = world * nb * args.steps / t_dev
+    value = job_throughput(world, nb, args.steps, t_dev)
 
     # per-kernel device times (same kernels, launched one by one between events)
     prof = []
@@ -359,7 +374,8 @@ def main():
         sim.step(1)
         _, _, _, s_cur = sim.get_state(x_h, v_h, f_h)
     e2e_s = time.perf_counter() - t0
-    e2e_val = world * nb * args.e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e_val = job_throughput(world, nb, args.e2e_steps, e2e_s)
     info = sim.info()
 
     pk = peaks()

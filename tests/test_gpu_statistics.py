@@ -1,0 +1,72 @@
+"""Long-run statistics of the GPU path against the FP64 oracle (same seed,
+same initial state; the trajectories decorrelate, the statistics must not).
+
+Bounds: time-averaged temperature within 1%; time-averaged E(k) within 5% per
+shell for k = 2..M/2 (k = 1 has too few modes).  The oracle's own spread
+between two seeds, measured with the same protocol, is 0.3% for T and 2.2%
+(largest shell) for E(k) at 6e4 steps, so the bounds leave room for noise
+but not for a missing or mis-scaled force term.
+"""
+import numpy as np
+import pytest
+
+from oracle import observables as ob
+from paper_1310_0998_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+L, ND, M = 32.0, 512, 32
+BASE = dict(a=25.0, gamma=4.5, kBT=1.0, rc=1.0, kbond=100.0, r0=0.5, dt=0.01)
+
+
+def _oracle(orc, seed, steps, every, burn, zeta, fp):
+    x, v = synth.dimers(ND, L, 0.5, seed=seed)
+    p = orc.params(L=L, fp=fp, zeta=zeta, seed=seed, **BASE)
+    st = orc.State(p, x, v, cells=True)
+    st.run(burn)
+    eps = ob.filter_width(L, ND, 10.0)
+    E, T = np.zeros(M // 2), []
+    n = 0
+    for _ in range((steps - burn) // every):
+        log = st.run(every, thermo=True)
+        T.append(2 * log[:, 0] / (2 * 2 * ND - 2))
+        c, vc = ob.agent_com(st.x, st.v, L)
+        E += ob.energy_spectrum(ob.velocity_field(c, vc, L, M, eps)[0])
+        n += 1
+    return E / n, float(np.mean(np.concatenate(T)))
+
+
+def _gpu(seed, steps, every, burn, zeta, fp):
+    from paper_1310_0998_gb300 import Sim
+    x, v = synth.dimers(ND, L, 0.5, seed=seed)
+    kw = dict(a=BASE["a"], gamma=BASE["gamma"], kBT=BASE["kBT"], rc=BASE["rc"], k_bond=BASE["kbond"],
+              r0=BASE["r0"], dt=BASE["dt"], f_p=fp, zeta=zeta, seed=seed)
+    E, T = np.zeros(M // 2), []
+    n = 0
+    with Sim(L, 2 * ND, **kw) as s:
+        s.set_positions(x, v)
+        s.step(burn)
+        for _ in range((steps - burn) // every):
+            s.step(every)
+            T.append(s.thermo_log(s.info().step - every + 1, every)[:, 3])
+            E += s.energy_spectrum(M)
+            n += 1
+    return E / n, float(np.mean(np.concatenate(T)))
+
+
+def test_active_run_statistics(orc):
+    """C1 (f_p = 1, zeta = 0.1): <T> and <E(k)> over steps 2e3..6e4."""
+    Eo, To = _oracle(orc, 1, 60000, 100, 2000, 0.1, 1.0)
+    Eg, Tg = _gpu(1, 60000, 100, 2000, 0.1, 1.0)
+    assert abs(Tg - To) <= 0.01 * To, (Tg, To)
+    rel = np.abs(Eg - Eo) / Eo
+    assert rel[1:].max() <= 0.05, rel
+
+
+def test_equilibrium_temperature(orc):
+    """zeta = f_p = 0: the GPU thermostat holds the oracle's <T> (= kBT up to
+    the time-step bias) within 1%."""
+    _, To = _oracle(orc, 3, 20000, 1000, 2000, 0.0, 0.0)
+    _, Tg = _gpu(3, 20000, 1000, 2000, 0.0, 0.0)
+    assert abs(Tg - To) <= 0.01 * To, (Tg, To)
+    assert abs(Tg - 1.0) <= 0.02
