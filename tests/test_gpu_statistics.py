@@ -2,10 +2,13 @@
 same initial state; the trajectories decorrelate, the statistics must not).
 
 Bounds: time-averaged temperature within 1%; time-averaged E(k) within 5% per
-shell for k = 2..M/2 (k = 1 has too few modes).  The oracle's own spread
-between two seeds, measured with the same protocol, is 0.3% for T and 2.2%
-(largest shell) for E(k) at 6e4 steps, so the bounds leave room for noise
-but not for a missing or mis-scaled force term.
+shell for k = 2..M/2 (k = 1 has too few modes), both averaged over three
+seeds on each side.  Measured with this protocol over six seeds, one run's
+E(k) scatters by 2-3% (k = 2, 3) down to 0.5% (k >= 9) about the seed mean,
+so a three-seed mean difference has a spread of at most ~1.6%: the 5% bound
+is three of those, and six-seed means of the two sides agree within 1.4% on
+every shell.  A missing or mis-scaled force term moves these statistics by
+far more.
 """
 import numpy as np
 import pytest
@@ -55,9 +58,12 @@ def _gpu(seed, steps, every, burn, zeta, fp):
 
 
 def test_active_run_statistics(orc):
-    """C1 (f_p = 1, zeta = 0.1): <T> and <E(k)> over steps 2e3..6e4."""
-    Eo, To = _oracle(orc, 1, 60000, 100, 2000, 0.1, 1.0)
-    Eg, Tg = _gpu(1, 60000, 100, 2000, 0.1, 1.0)
+    """C1 (f_p = 1, zeta = 0.1): <T> and <E(k)> over steps 2e3..6e4, seeds
+    1-3 on both sides."""
+    o = [_oracle(orc, s, 60000, 100, 2000, 0.1, 1.0) for s in (1, 2, 3)]
+    g = [_gpu(s, 60000, 100, 2000, 0.1, 1.0) for s in (1, 2, 3)]
+    Eo, To = np.mean([e for e, _ in o], axis=0), float(np.mean([t for _, t in o]))
+    Eg, Tg = np.mean([e for e, _ in g], axis=0), float(np.mean([t for _, t in g]))
     assert abs(Tg - To) <= 0.01 * To, (Tg, To)
     rel = np.abs(Eg - Eo) / Eo
     assert rel[1:].max() <= 0.05, rel
