@@ -188,6 +188,33 @@ def ensemble_leg(R, steps, warmup, seed=0):
             "timing": "wall clock around each leg, synchronised; sequential = each replica alone, one after another"}
 
 
+OPS_PER_BEAD_STEP_3D = 1200.0   # 40.5 half-stencil tests x 10 + 6.3 pairs x 115 + 70 integration
+
+
+def three_d_leg(steps=20, warmup=3, L=64.0, seed=0):
+    """Three-dimensional variant: density-3 cube of side L (3 L^3 beads), the
+    C3 parameters; wall clock around `steps` synchronised steps."""
+    from paper_1310_0998_gb300 import Sim3, synth
+    nb = int(3 * L ** 3) // 2 * 2
+    x, v = synth.dimers3(nb // 2, L, PHYS["r0"], seed=seed)
+    with Sim3(L, nb, seed=seed, a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"], rc=PHYS["rc"],
+              k_bond=PHYS["kbond"], r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"], dt=PHYS["dt"]) as s:
+        s.set_positions(x, v)
+        s.step(warmup)
+        s.sync()
+        t0 = time.perf_counter()
+        s.step(steps)
+        s.sync()
+        dt = time.perf_counter() - t0
+    rate = nb * steps / dt
+    pk = peaks()
+    alu_peak = N_SM * LANES * pk["sm_max_mhz"] * 1e6
+    return {"beads": nb, "L": L, "steps": steps, "particle_steps_per_s": rate, "ms_per_step": 1e3 * dt / steps,
+            "roofline": {"bound": "alu", "achieved": OPS_PER_BEAD_STEP_3D * rate / 1e12, "peak": alu_peak / 1e12,
+                         "unit": "Tops/s", "frac": OPS_PER_BEAD_STEP_3D * rate / alu_peak},
+            "timing": "wall clock around synchronised steps (scan, scatter, force per step)"}
+
+
 def surrogate_leg(n_train=64, n_test=16, seed=0):
     """Learned surrogate, scaled-down version of the paper-point study:
     statistics of n_train + n_test parameter points (area fraction U(0.1, 0.6),
@@ -280,6 +307,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
+    ap.add_argument("--no-3d", action="store_true", help="skip the three-dimensional leg")
     ap.add_argument("--wexp", type=float, default=0.0,
                     help="exponent s of w in the dissipative/random forces (0 = 2, the printed form)")
     ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue, 3 grid-order queue")
@@ -411,6 +439,8 @@ def main():
         line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup)
     if rank == 0 and not args.no_surrogate:
         line["surrogate"] = surrogate_leg()
+    if rank == 0 and not args.no_3d:
+        line["three_d"] = three_d_leg()
     if rank == 0 and not args.no_cpu:
         Lc = 128.0 if nb > 200000 else L
         nbc = int(round(nb * (Lc / L) ** 2)) // 2 * 2

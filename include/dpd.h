@@ -269,6 +269,37 @@ int dpd_batch_barrier_selftest(dpd_batch *b);
 int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
 
 /* ------------------------------------------------------------------------
+ * Three-dimensional variant.  Sec. 2 states every force as a vector law; the
+ * same pair force, bond, propulsion, drag and velocity-Verlet step (Sec. 5)
+ * in a periodic cube of side p->L (fixed-point positions per axis, n_c^3
+ * cells of side L / n_c >= r_c).  The paper itself simulates two dimensions.
+ * All of dpd_params applies (tile and variant are ignored).  Host pointers.
+ * ------------------------------------------------------------------------ */
+typedef struct dpd3_ctx dpd3_ctx;
+
+/* Create on the current device (about 190 bytes per bead plus 8 per cell). */
+int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out);
+void dpd3_destroy(dpd3_ctx *ctx);
+
+/* Set positions x [N][3] (any, wrapped into the cube and rounded to L 2^-32)
+ * and velocities v [N][3] in id order at step `step`, and compute the set-up
+ * force F(x, v, step).  Non-finite input gives DPD_ERR_NONFINITE.
+ * Synchronises. */
+int dpd3_set_state(dpd3_ctx *ctx, const double *x, const float *v, int64_t step);
+
+/* Advance n velocity-Verlet steps (asynchronous; errors latched). */
+int dpd3_step(dpd3_ctx *ctx, int64_t n);
+int dpd3_sync(dpd3_ctx *ctx);
+
+/* Canonical state in id order: x [N][3] (exact X L / 2^32), v, f [N][3].
+ * Synchronises. */
+int dpd3_get_state(dpd3_ctx *ctx, double *x, float *v, float *f, int64_t *step);
+
+/* FP64 reductions of the current step: KE = m/2 sum |v|^2, P = m sum v,
+ * T = m sum |v|^2 / (3N - 3); out = (KE, Px, Py, Pz, T).  Synchronises. */
+int dpd3_thermo(dpd3_ctx *ctx, double out[5]);
+
+/* ------------------------------------------------------------------------
  * Learned surrogate of ensemble statistics (not part of the paper: a model
  * of this simulator's own outputs).  A deep ensemble of K MLPs
  * 4 -> 256 -> 256 -> 40 (SiLU hidden layers, linear output), BF16 weights and

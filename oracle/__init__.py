@@ -85,6 +85,9 @@ def lib():
             L.orc_pair_counts.argtypes = [P(OrcParams), i64, vp, d, vp, vp]
             L.orc_pair_counts.restype = i64
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc3_forces.argtypes = [P(OrcParams), i64, vp, vp, i64, vp]
+            L.orc3_forces.restype = i64
+            L.orc3_run.argtypes = [P(OrcParams), i64, vp, vp, vp, P(i64), i64, vp]
             _lib = L
     return _lib
 
@@ -156,6 +159,37 @@ class State:
                       self.v.ctypes.data_as(ctypes.c_void_p), self.f.ctypes.data_as(ctypes.c_void_p),
                       ctypes.byref(st), int(nsteps), int(self.cells),
                       log.ctypes.data_as(ctypes.c_void_p) if thermo else None)
+        self.step = st.value
+        return log[:nsteps] if thermo else None
+
+
+def forces3(p: OrcParams, x, v, step: int):
+    """Three-dimensional variant: total force on every bead in the periodic
+    cube of side p.L; returns (f [n,3], interacting pairs)."""
+    x, xp = _c(x, np.float64)
+    v, vp = _c(v, np.float64)
+    f = np.zeros((x.shape[0], 3), np.float64)
+    npairs = lib().orc3_forces(ctypes.byref(p), x.shape[0], xp, vp, int(step), f.ctypes.data_as(ctypes.c_void_p))
+    return f, int(npairs)
+
+
+class State3:
+    """Velocity-Verlet state of the three-dimensional variant, FP64, all pairs."""
+
+    def __init__(self, p: OrcParams, x, v, step: int = 0):
+        self.p = p
+        self.x = np.array(x, np.float64, copy=True, order="C")
+        self.v = np.array(v, np.float64, copy=True, order="C")
+        self.step = int(step)
+        self.f, _ = forces3(p, self.x, self.v, self.step)
+
+    def run(self, nsteps: int, thermo: bool = False):
+        """Advance nsteps steps; optional per-step (KE, Px, Py, Pz, 0) log."""
+        st = ctypes.c_int64(self.step)
+        log = np.zeros((max(nsteps, 1), 5), np.float64) if thermo else None
+        lib().orc3_run(ctypes.byref(self.p), self.x.shape[0], self.x.ctypes.data_as(ctypes.c_void_p),
+                       self.v.ctypes.data_as(ctypes.c_void_p), self.f.ctypes.data_as(ctypes.c_void_p),
+                       ctypes.byref(st), int(nsteps), log.ctypes.data_as(ctypes.c_void_p) if thermo else None)
         self.step = st.value
         return log[:nsteps] if thermo else None
 

@@ -31,6 +31,8 @@
  *   orc_cell_counts     the cell-binning rule that the GPU path documents,
  *                       floor(x n_c / L) on the fixed-point position grid.
  *   orc_pair_counts     brute-force per-bead interacting-neighbour counts.
+ *   orc3_forces,        the same force laws and velocity-Verlet in a periodic
+ *   orc3_run            cube (three-dimensional variant), all pairs.
  *
  * Parity pins (tests/test_oracle_*.py): Philox against Triton's independent
  * Philox4x32-10 and against uniformity statistics; pair force against
@@ -372,4 +374,102 @@ int orc_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Three-dimensional variant.  Sec. 2 writes every force as a vector law, so  */
+/* the same Eqs. (DPDf), (DPDcdr), (weightFunc01), (stiffSpring), (DPDnp)     */
+/* apply unchanged in a periodic cube of side L; x, v, f: [n][3] doubles.     */
+/* ------------------------------------------------------------------------ */
+static int pair_force3(const orc_params *p, const double d[3], const double dv[3], uint32_t i, uint32_t j,
+                       int64_t step, double F3[3])
+{
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < p->rc * p->rc) || r2 == 0.0) return 0;
+    double r = sqrt(r2);
+    double w = 1.0 - r / p->rc;
+    double e[3] = {d[0] / r, d[1] / r, d[2] / r};
+    double dve = dv[0] * e[0] + dv[1] * e[1] + dv[2] * e[2];
+    double sigma = sqrt(2.0 * p->gamma * p->kBT);
+    double alpha = orc_alpha(i, j, step, p->seed, p->replica, p->noise);
+    double s = p->wexp > 0.0 ? p->wexp : 2.0;
+    double wd = s == 2.0 ? w * w : pow(w, s);
+    double wr = s == 2.0 ? w : pow(w, 0.5 * s);
+    double F = p->a * w - p->gamma * wd * dve + sigma * wr * alpha / sqrt(p->dt);
+    for (int c = 0; c < 3; ++c) F3[c] = F * e[c];
+    return 1;
+}
+
+static void bonded_and_external3(const orc_params *p, int64_t n, const double *x, const double *v, double *f)
+{
+    for (int64_t k = 0; k < n / 2; ++k) {
+        int64_t i = 2 * k, j = 2 * k + 1;
+        double d[3], r2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = minimg(x[3 * i + c] - x[3 * j + c], p->L);
+            r2 += d[c] * d[c];
+        }
+        double r = sqrt(r2);
+        if (r > 0.0) {
+            double fb = -p->kbond * (r - p->r0);
+            for (int c = 0; c < 3; ++c) {
+                double nc = d[c] / r;
+                f[3 * i + c] += fb * nc + p->fp * nc;
+                f[3 * j + c] += -fb * nc + p->fp * nc;
+            }
+        }
+    }
+    for (int64_t k = 0; k < 3 * n; ++k) f[k] -= p->zeta * v[k];
+}
+
+int64_t orc3_forces(const orc_params *p, int64_t n, const double *x, const double *v, int64_t step, double *f)
+{
+    int64_t npairs = 0;
+    memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            if (p->exclude_bonded && (i ^ 1) == j) continue;
+            double d[3], dv[3], F3[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = minimg(x[3 * i + c] - x[3 * j + c], p->L);
+                dv[c] = v[3 * i + c] - v[3 * j + c];
+            }
+            if (pair_force3(p, d, dv, (uint32_t)i, (uint32_t)j, step, F3)) {
+                for (int c = 0; c < 3; ++c) {
+                    f[3 * i + c] += F3[c];
+                    f[3 * j + c] -= F3[c];
+                }
+                ++npairs;
+            }
+        }
+    bonded_and_external3(p, n, x, v, f);
+    return npairs;
+}
+
+/* Velocity-Verlet in the cube, as orc_run; thermo per step: (KE, Px, Py, Pz,
+ * 0). */
+void orc3_run(const orc_params *p, int64_t n, double *x, double *v, double *f, int64_t *step, int64_t nsteps,
+              double *thermo)
+{
+    double h = 0.5 * p->dt / p->mass;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int64_t k = 0; k < 3 * n; ++k) v[k] += h * f[k];
+        for (int64_t k = 0; k < 3 * n; ++k) {
+            x[k] += p->dt * v[k];
+            x[k] -= p->L * floor(x[k] / p->L);
+        }
+        *step += 1;
+        orc3_forces(p, n, x, v, *step, f);
+        for (int64_t k = 0; k < 3 * n; ++k) v[k] += h * f[k];
+        if (thermo) {
+            double ke = 0, P[3] = {0, 0, 0};
+            for (int64_t i = 0; i < n; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    ke += 0.5 * p->mass * v[3 * i + c] * v[3 * i + c];
+                    P[c] += p->mass * v[3 * i + c];
+                }
+            thermo[5 * s + 0] = ke; thermo[5 * s + 1] = P[0]; thermo[5 * s + 2] = P[1];
+            thermo[5 * s + 3] = P[2]; thermo[5 * s + 4] = 0.0;
+        }
+    }
 }

@@ -6,14 +6,16 @@ input generator (``synth``) does not load the CUDA library.
 """
 import importlib
 
-__all__ = ["Sim", "Ensemble", "make_params", "synth"]
+__all__ = ["Sim", "Sim3", "Ensemble", "Surrogate", "make_params", "synth"]
 
 
 def __getattr__(name):
-    if name in ("Sim", "make_params"):
+    if name in ("Sim", "Sim3", "make_params"):
         return getattr(importlib.import_module(__name__ + ".sim"), name)
+    if name == "Surrogate":
+        return importlib.import_module(__name__ + ".surrogate").Surrogate
     if name == "Ensemble":
         return importlib.import_module(__name__ + ".ensemble").Ensemble
-    if name in ("synth", "sim", "build", "ensemble"):
+    if name in ("synth", "sim", "build", "ensemble", "surrogate", "study"):
         return importlib.import_module(__name__ + "." + name)
     raise AttributeError(name)

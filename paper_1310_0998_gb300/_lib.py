@@ -103,6 +103,13 @@ def _declare(L):
         "dpd_batch_sync": ([vp], c_int),
         "dpd_batch_barrier_selftest": ([vp], c_int),
         "dpd_batch_info": ([vp, P(c_int), P(c_int), P(c_int)], c_int),
+        "dpd3_create": ([P(DpdParams), vp, P(vp)], c_int),
+        "dpd3_destroy": ([vp], None),
+        "dpd3_set_state": ([vp, vp, vp, i64], c_int),
+        "dpd3_step": ([vp, i64], c_int),
+        "dpd3_sync": ([vp], c_int),
+        "dpd3_get_state": ([vp, vp, vp, vp, P(i64)], c_int),
+        "dpd3_thermo": ([vp, vp], c_int),
         "sur_create": ([c_int, c_int, u64, vp, P(vp)], c_int),
         "sur_destroy": ([vp], None),
         "sur_set_weights": ([vp, c_int, vp, vp, vp, vp, vp, vp], c_int),

@@ -1,0 +1,416 @@
+// Three-dimensional variant of the simulator (include/dpd.h, dpd3_*).
+//
+// Sec. 2 states every force as a vector law, so the pair force (Eqs. DPDf,
+// DPDcdr, weightFunc01), the bond (Eq. stiffSpring), propulsion and drag
+// (Eq. DPDnp) and the velocity-Verlet step of Sec. 5 carry over to a periodic
+// cube unchanged; only the geometry is new.  Positions are 32-bit fixed point
+// per axis as in two dimensions (uniform resolution, wrap by overflow, exact
+// minimum image and cell index).
+//
+// Layout (N beads, n_c^3 cells numbered (z n_c + y) n_c + x):
+//   S_p  uint4[N]   (X, Y, Z, id) of the pre-force state, sorted by cell
+//   S_v  float4[N]  the half-step velocity v_{s-1/2} (v_s at set-up)
+//   U_p, U_v, U_rank  the next pre-force state in the order of S, with each
+//                     bead's rank inside its new cell (atomic ticket)
+//   slot u32[N]     id -> sorted slot (the bonded partner of bead id is id^1)
+//   counts, cstart  cell populations and their exclusive scan (the same
+//                   decoupled look-back scan as the 2D path)
+//   C_p, C_v, C_f   canonical (X_s, v_s, f_s) in id order after each call
+// One step: scan, scatter, then one thread per bead walks the full 3x3x3
+// stencil (every pair is evaluated from both sides with the same random
+// number, so the forces are antisymmetric bit for bit), adds bond,
+// propulsion and drag, does the second half-kick, the FP64 thermo partials,
+// the next half-kick and drift, and bins the new position.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dpd.h"
+#include "sim_host.h"
+#include "sim_kernels.cuh"
+
+namespace dpd {
+
+struct Sys3 {
+    Sys b;                      // geometry scalars, physics, keys, scan/thermo/error words
+    uint4 *S_p, *U_p, *C_p;
+    float4 *S_v, *U_v, *C_v, *C_f;
+    uint32_t *U_rank, *slot;
+};
+
+__device__ __forceinline__ int cell3(const Sys &d, uint32_t X, uint32_t Y, uint32_t Z)
+{
+    return (cell_coord(d, Z) * d.nc + cell_coord(d, Y)) * d.nc + cell_coord(d, X);
+}
+
+__global__ void k3_scan(Sys d, int nblocks) { scan_decoupled(d, nblocks); }
+
+__global__ void k3_bin(Sys3 s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.b.n) return;
+    const uint4 p = s.U_p[k];
+    s.U_rank[k] = atomicAdd(&s.b.counts[cell3(s.b, p.x, p.y, p.z)], 1u);
+}
+
+__global__ void k3_scatter(Sys3 s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.b.n) return;
+    const uint4 p = s.U_p[k];
+    const uint32_t dst = s.b.cstart[cell3(s.b, p.x, p.y, p.z)] + s.U_rank[k];
+    if (dst >= (uint32_t)s.b.n || p.w >= (uint32_t)s.b.n) {
+        set_err_at(s.b, ERR_INTERNAL, 11, k, dst, p.w);
+        return;
+    }
+    s.S_p[dst] = p;
+    s.S_v[dst] = s.U_v[k];
+    s.slot[p.w] = dst;
+}
+
+// Double positions [N][3] and float velocities [N][3] (id order) -> U.
+__global__ void k3_load(Sys3 s, const double *__restrict__ x, const float *__restrict__ v)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.b.n) return;
+    uint32_t X[3];
+    bool ok = true;
+    for (int c = 0; c < 3; ++c) {
+        const double u = x[3 * k + c] * s.b.inv_ulen_d;
+        if (!(fabs(u) < 4503599627370496.0)) { ok = false; X[c] = 0u; }
+        else X[c] = (uint32_t)(unsigned long long)llrint(u);
+    }
+    float4 vv = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 0.f);
+    if (!isfinite(vv.x) || !isfinite(vv.y) || !isfinite(vv.z)) ok = false;
+    if (!ok) {
+        set_err(s.b, ERR_NONFINITE);
+        vv = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    s.U_p[k] = make_uint4(X[0], X[1], X[2], (uint32_t)k);
+    s.U_v[k] = vv;
+}
+
+__global__ void k3_store(Sys3 s, double *__restrict__ x, float *__restrict__ v, float *__restrict__ f)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.b.n) return;
+    const uint4 p = s.C_p[k];
+    const float4 vv = s.C_v[k], ff = s.C_f[k];
+    x[3 * k] = (double)p.x * s.b.ulen_d;
+    x[3 * k + 1] = (double)p.y * s.b.ulen_d;
+    x[3 * k + 2] = (double)p.z * s.b.ulen_d;
+    v[3 * k] = vv.x; v[3 * k + 1] = vv.y; v[3 * k + 2] = vv.z;
+    f[3 * k] = ff.x; f[3 * k + 1] = ff.y; f[3 * k + 2] = ff.z;
+}
+
+__global__ void k3_set_step(Sys d, long long s) { *d.step = s; }
+
+// Pair force magnitude along e (as the 2D pair term, with dv.e in 3D).
+__device__ __forceinline__ float pair_scalar3(const Sys &d, float r2, float rinv, float dve, uint32_t ia,
+                                              uint32_t ib, uint32_t s_lo, uint32_t s_hi)
+{
+    const float r = r2 * rinv;
+    const float w = 1.0f - r * d.inv_rc;
+    const float nz = pair_noise(d, ia, ib, s_lo, s_hi);
+    if (!d.gen_w) return w * (d.a - d.gamma * w * dve + d.sig_r * nz);
+    const float wr = __powf(w, d.hwexp);
+    return d.a * w - d.gamma * (wr * wr) * dve + d.sig_r * wr * nz;
+}
+
+__global__ void __launch_bounds__(256) k3_force(Sys3 s, int flags)
+{
+    const Sys &d = s.b;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    float ke = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+    if (g < d.n) {
+        const long long step = *d.step;
+        const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
+        const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+        const uint4 pi = s.S_p[g];
+        const float4 vi = s.S_v[g];
+        const uint32_t id = pi.w, pid = d.excl ? (id ^ 1u) : 0xffffffffu;
+        const uint32_t n = (uint32_t)d.n;
+        const int cx = cell_coord(d, pi.x), cy = cell_coord(d, pi.y), cz = cell_coord(d, pi.z);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int oz = -1; oz <= 1; ++oz) {
+            int z = cz + oz;
+            z += z < 0 ? d.nc : (z >= d.nc ? -d.nc : 0);
+            for (int oy = -1; oy <= 1; ++oy) {
+                int y = cy + oy;
+                y += y < 0 ? d.nc : (y >= d.nc ? -d.nc : 0);
+                const int row = (z * d.nc + y) * d.nc;
+                for (int ox = -1; ox <= 1; ++ox) {
+                    int x = cx + ox;
+                    x += x < 0 ? d.nc : (x >= d.nc ? -d.nc : 0);
+                    const int c = row + x;
+                    const uint32_t b = min(d.cstart[c], n), e = min(max(d.cstart[c + 1], b), n);
+                    for (uint32_t q = b; q < e; ++q) {
+                        if (q == (uint32_t)g) continue;
+                        const uint4 pj = s.S_p[q];
+                        if (pj.w == pid) continue;
+                        const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < d.rc2 && r2 > 0.f) {
+                            const float4 vj = s.S_v[q];
+                            const float rinv = rsqrtf(r2);
+                            const float ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;   // e = (x_i - x_j)/r
+                            const float dve = (vi.x - vj.x) * ex + (vi.y - vj.y) * ey + (vi.z - vj.z) * ez;
+                            const float F = pair_scalar3(d, r2, rinv, dve, id, pj.w, s_lo, s_hi);
+                            fx += F * ex;
+                            fy += F * ey;
+                            fz += F * ez;
+                        }
+                    }
+                }
+            }
+        }
+        // bond and propulsion (partner id ^ 1), drag on the half-step velocity
+        const uint32_t ps = s.slot[id ^ 1u];
+        if (ps < n) {
+            const uint4 pp = s.S_p[ps];
+            const float dx = mdiff(d, pi.x, pp.x), dy = mdiff(d, pi.y, pp.y), dz = mdiff(d, pi.z, pp.z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > 0.f) {
+                const float r = sqrtf(r2), inv = 1.0f / r;
+                const float fb = -d.kbond * (r - d.r0);
+                const float sp = (id & 1u) ? -d.fp : d.fp;   // n_k = head - tail
+                fx += (fb + sp) * dx * inv;
+                fy += (fb + sp) * dy * inv;
+                fz += (fb + sp) * dz * inv;
+            }
+        } else {
+            set_err_at(d, ERR_INTERNAL, 12, g, id, ps);
+        }
+        float vx = vi.x, vy = vi.y, vz = vi.z;
+        fx -= d.zeta * vx;
+        fy -= d.zeta * vy;
+        fz -= d.zeta * vz;
+        if (!(flags & F_FIRST)) { vx += d.hdtm * fx; vy += d.hdtm * fy; vz += d.hdtm * fz; }
+        ke = vx * vx + vy * vy + vz * vz;
+        px = vx; py = vy; pz = vz;
+        if (flags & F_FINAL) {
+            s.C_p[id] = make_uint4(pi.x, pi.y, pi.z, 0u);
+            s.C_v[id] = make_float4(vx, vy, vz, 0.f);
+            s.C_f[id] = make_float4(fx, fy, fz, 0.f);
+        }
+        if (flags & F_ADVANCE) {
+            vx += d.hdtm * fx;
+            vy += d.hdtm * fy;
+            vz += d.hdtm * fz;
+            const float ddx = d.dt * vx, ddy = d.dt * vy, ddz = d.dt * vz;
+            uint32_t nx = pi.x, ny = pi.y, nz = pi.z;
+            const float lim = 0.25f * d.L;
+            if (fabsf(ddx) < lim && fabsf(ddy) < lim && fabsf(ddz) < lim) {   // false for NaN too
+                nx = fx_add(d, pi.x, ddx);
+                ny = fx_add(d, pi.y, ddy);
+                nz = fx_add(d, pi.z, ddz);
+            } else {
+                set_err(d, ERR_NONFINITE);
+                vx = vy = vz = 0.f;
+            }
+            s.U_rank[g] = atomicAdd(&d.counts[cell3(d, nx, ny, nz)], 1u);
+            s.U_p[g] = make_uint4(nx, ny, nz, id);
+            s.U_v[g] = make_float4(vx, vy, vz, 0.f);
+        }
+    }
+    // thermo partials: FP32 within a warp, FP64 across warps and blocks
+    if (flags & (F_ADVANCE | F_FINAL)) {
+        for (int o = 16; o > 0; o >>= 1) {
+            ke += __shfl_xor_sync(0xffffffffu, ke, o);
+            px += __shfl_xor_sync(0xffffffffu, px, o);
+            py += __shfl_xor_sync(0xffffffffu, py, o);
+            pz += __shfl_xor_sync(0xffffffffu, pz, o);
+        }
+        __shared__ double red[8][4];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) { red[wid][0] = ke; red[wid][1] = px; red[wid][2] = py; red[wid][3] = pz; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a[4] = {0, 0, 0, 0};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                for (int c = 0; c < 4; ++c) a[c] += red[w][c];
+            double *t = d.thermo + 4 * (size_t)(*d.step % THERMO_CAP);
+            for (int c = 0; c < 4; ++c) atomicAdd(&t[c], a[c]);
+        }
+    }
+}
+
+}  // namespace dpd
+
+using namespace dpd;
+
+struct dpd3_ctx {
+    dpd_params p{};
+    Sys3 s{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int nscan = 1;
+    void *pool = nullptr;
+    char *stage = nullptr;     // 48 B/bead staging for host state transfers
+    double *h_pin = nullptr;
+    long long step = 0;
+    bool have_state = false;
+};
+
+#define CU3(x)                                                                      \
+    do {                                                                            \
+        const cudaError_t e_ = (x);                                                 \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? DPD_ERR_OOM : DPD_ERR_CUDA; \
+    } while (0)
+
+static int latched3(dpd3_ctx *c)
+{
+    int *e = (int *)(c->h_pin + 500);
+    CU3(cudaMemcpyAsync(e, c->s.b.err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU3(cudaStreamSynchronize(c->st));
+    if (*e & ERR_NONFINITE) return DPD_ERR_NONFINITE;
+    if (*e & ERR_TIMEOUT) return DPD_ERR_TIMEOUT;
+    if (*e & ERR_INTERNAL) return DPD_ERR_INTERNAL;
+    return DPD_OK;
+}
+
+static void iteration3(dpd3_ctx *c, int flags)
+{
+    const int g = (c->s.b.n + 255) / 256;
+    k3_scan<<<c->nscan, SCAN_NT, 0, c->st>>>(c->s.b, c->nscan);
+    k3_scatter<<<g, 256, 0, c->st>>>(c->s);
+    k3_force<<<g, 256, 0, c->st>>>(c->s, flags);
+}
+
+extern "C" {
+
+int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
+{
+    if (!out) return DPD_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    const int nc = n_cells_side(p->L, p->rc);
+    if ((double)nc * nc * nc >= 2.0e9) return DPD_ERR_INVALID_ARG;
+    dpd3_ctx *c = new (std::nothrow) dpd3_ctx();
+    if (!c) return DPD_ERR_OOM;
+    c->p = *p;
+    if (stream) c->st = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return DPD_ERR_CUDA; }
+        c->own_stream = true;
+    }
+    Sys &d = c->s.b;
+    fill_physics(d, p);
+    fill_geometry(d, p, 8);
+    d.ncells = nc * nc * nc;
+    d.ntx = 0;
+    d.cap = 0;
+    c->nscan = (d.ncells + SCAN_TILE - 1) / SCAN_TILE;
+    const size_t n = (size_t)d.n, nce = (size_t)d.ncells;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_Sp = take(16 * n), o_Sv = take(16 * n), o_Up = take(16 * n), o_Uv = take(16 * n),
+                 o_Cp = take(16 * n), o_Cv = take(16 * n), o_Cf = take(16 * n), o_rank = take(4 * n),
+                 o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
+                 o_th = take(32 * (size_t)THERMO_CAP), o_step = take(8), o_err = take(4), o_einfo = take(32),
+                 o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(48 * n);
+    if (cudaMalloc(&c->pool, off) != cudaSuccess || cudaMallocHost((void **)&c->h_pin, 4096) != cudaSuccess) {
+        dpd3_destroy(c);
+        return DPD_ERR_OOM;
+    }
+    char *b = (char *)c->pool;
+    c->s.S_p = (uint4 *)(b + o_Sp); c->s.S_v = (float4 *)(b + o_Sv);
+    c->s.U_p = (uint4 *)(b + o_Up); c->s.U_v = (float4 *)(b + o_Uv);
+    c->s.C_p = (uint4 *)(b + o_Cp); c->s.C_v = (float4 *)(b + o_Cv); c->s.C_f = (float4 *)(b + o_Cf);
+    c->s.U_rank = (uint32_t *)(b + o_rank); c->s.slot = (uint32_t *)(b + o_slot);
+    d.slot = c->s.slot;
+    d.counts = (uint32_t *)(b + o_cnt); d.cstart = (uint32_t *)(b + o_cst);
+    d.thermo = (double *)(b + o_th); d.step = (long long *)(b + o_step);
+    d.err = (int *)(b + o_err); d.errinfo = (long long *)(b + o_einfo);
+    d.scan_status = (unsigned long long *)(b + o_ss); d.scan_ticket = (unsigned long long *)(b + o_tk);
+    d.S_xv = nullptr; d.S_id = nullptr; d.U_xv = nullptr; d.U_id = nullptr; d.U_rank = c->s.U_rank;
+    d.C_xv = nullptr; d.C_f = nullptr; d.pcnt = nullptr; d.ovf = nullptr;
+    c->stage = b + o_stage;
+    if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess || cudaStreamSynchronize(c->st) != cudaSuccess) {
+        dpd3_destroy(c);
+        return DPD_ERR_CUDA;
+    }
+    *out = c;
+    return DPD_OK;
+}
+
+void dpd3_destroy(dpd3_ctx *c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->pool) cudaFree(c->pool);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+int dpd3_set_state(dpd3_ctx *c, const double *x, const float *v, int64_t step)
+{
+    if (!c || !x || !v) return DPD_ERR_INVALID_ARG;
+    const size_t n = (size_t)c->s.b.n;
+    char *st = c->stage;
+    CU3(cudaMemcpyAsync(st, x, 24 * n, cudaMemcpyHostToDevice, c->st));
+    CU3(cudaMemcpyAsync(st + 24 * n, v, 12 * n, cudaMemcpyHostToDevice, c->st));
+    CU3(cudaMemsetAsync(c->s.b.err, 0, sizeof(int), c->st));
+    CU3(cudaMemsetAsync(c->s.b.errinfo, 0, 32, c->st));
+    CU3(cudaMemsetAsync(c->s.b.counts, 0, 4 * (size_t)c->s.b.ncells, c->st));
+    const int g = (int)((n + 255) / 256);
+    k3_load<<<g, 256, 0, c->st>>>(c->s, (const double *)st, (const float *)(st + 24 * n));
+    k3_bin<<<g, 256, 0, c->st>>>(c->s);
+    k3_set_step<<<1, 1, 0, c->st>>>(c->s.b, step - 1);
+    iteration3(c, F_FIRST | F_FINAL | F_ADVANCE);
+    CU3(cudaGetLastError());
+    c->step = step;
+    c->have_state = true;
+    return latched3(c);
+}
+
+int dpd3_step(dpd3_ctx *c, int64_t n)
+{
+    if (!c || n < 0) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    for (int64_t i = 0; i < n; ++i) iteration3(c, i == n - 1 ? (F_ADVANCE | F_FINAL) : F_ADVANCE);
+    CU3(cudaGetLastError());
+    c->step += n;
+    return DPD_OK;
+}
+
+int dpd3_sync(dpd3_ctx *c)
+{
+    if (!c) return DPD_ERR_INVALID_ARG;
+    return latched3(c);
+}
+
+int dpd3_get_state(dpd3_ctx *c, double *x, float *v, float *f, int64_t *step)
+{
+    if (!c || !x || !v || !f) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    const size_t n = (size_t)c->s.b.n;
+    double *dx = (double *)c->stage;
+    float *dv = (float *)(dx + 3 * n), *df = dv + 3 * n;
+    k3_store<<<(int)((n + 255) / 256), 256, 0, c->st>>>(c->s, dx, dv, df);
+    CU3(cudaMemcpyAsync(x, dx, 24 * n, cudaMemcpyDeviceToHost, c->st));
+    CU3(cudaMemcpyAsync(v, dv, 12 * n, cudaMemcpyDeviceToHost, c->st));
+    CU3(cudaMemcpyAsync(f, df, 12 * n, cudaMemcpyDeviceToHost, c->st));
+    if (step) *step = c->step;
+    return latched3(c);
+}
+
+int dpd3_thermo(dpd3_ctx *c, double out[5])
+{
+    if (!c || !out) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    CU3(cudaMemcpyAsync(c->h_pin, c->s.b.thermo + 4 * (size_t)(c->step % THERMO_CAP), 32, cudaMemcpyDeviceToHost,
+                        c->st));
+    const int rc = latched3(c);
+    const double m = c->p.mass, n = (double)c->s.b.n;
+    out[0] = 0.5 * m * c->h_pin[0];
+    out[1] = m * c->h_pin[1];
+    out[2] = m * c->h_pin[2];
+    out[3] = m * c->h_pin[3];
+    out[4] = m * c->h_pin[0] / (3.0 * n - 3.0);
+    return rc;
+}
+
+}  // extern "C"

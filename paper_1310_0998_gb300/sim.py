@@ -176,3 +176,58 @@ class Sim:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Sim3:
+    """Three-dimensional variant: one periodic cube of N beads (wraps dpd3_*)."""
+
+    def __init__(self, L: float, n_beads: int, stream=None, **params):
+        self._lib = _lib.lib()
+        self.L, self.n = float(L), int(n_beads)
+        self._p = make_params(L, n_beads, **params)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(int(stream)) if stream else None
+        check(self._lib.dpd3_create(ctypes.byref(self._p), st, ctypes.byref(h)), "dpd3_create")
+        self._h = h
+
+    def set_positions(self, x, v=None, step: int = 0):
+        x = np.ascontiguousarray(x, np.float64)
+        v = np.zeros((self.n, 3), np.float32) if v is None else np.ascontiguousarray(v, np.float32)
+        check(self._lib.dpd3_set_state(self._h, ptr(x), ptr(v), int(step)), "dpd3_set_state")
+
+    def step(self, n: int = 1):
+        check(self._lib.dpd3_step(self._h, int(n)), "dpd3_step")
+
+    def sync(self):
+        check(self._lib.dpd3_sync(self._h), "dpd3_sync")
+
+    def get_state(self):
+        x = np.zeros((self.n, 3), np.float64)
+        v = np.zeros((self.n, 3), np.float32)
+        f = np.zeros((self.n, 3), np.float32)
+        st = ctypes.c_int64()
+        check(self._lib.dpd3_get_state(self._h, ptr(x), ptr(v), ptr(f), ctypes.byref(st)), "dpd3_get_state")
+        return x, v, f, st.value
+
+    def thermo(self):
+        """(KE, Px, Py, Pz, T) of the current step, FP64."""
+        out = np.zeros(5, np.float64)
+        check(self._lib.dpd3_thermo(self._h, ptr(out)), "dpd3_thermo")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.dpd3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -72,6 +72,26 @@ def velocities(n_beads: int, scale: float, seed: int = 1):
     return (rng.standard_normal((n_beads, 2)) * scale).astype(np.float32)
 
 
+def dimers3(n_dimers: int, L: float, r0: float, seed: int = 0):
+    """Three-dimensional variant: centres uniform in the periodic cube,
+    orientations uniform on the unit sphere, zero velocities.
+    Returns (x [2n,3] float64 on the grid in [0,L), v [2n,3] float32 zeros)."""
+    rng = np.random.default_rng(seed)
+    c = rng.random((n_dimers, 3)) * L
+    u = rng.standard_normal((n_dimers, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    h = 0.5 * r0 * u
+    x = np.empty((2 * n_dimers, 3), np.float64)
+    x[0::2] = c + h
+    x[1::2] = c - h
+    return on_grid(x, L), np.zeros((2 * n_dimers, 3), np.float32)
+
+
+def velocities3(n_beads: int, scale: float, seed: int = 1):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((n_beads, 3)) * scale).astype(np.float32)
+
+
 def uniform_beads(n_beads: int, L: float, seed: int = 0):
     """Beads uniformly in the box (any pairing), on the grid."""
     rng = np.random.default_rng(seed)
