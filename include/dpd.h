@@ -337,8 +337,20 @@ int sur_gradients(sur_ctx *s, int member, const float *X, const float *Y, int n,
 int sur_train(sur_ctx *s, const float *X, const float *Y, int n, int epochs, int batch, float lr, float *final_loss);
 
 /* Ensemble mean Y [n][40] and member standard deviation spread [n][40]
- * (may be NULL), in output units. */
+ * (may be NULL), in output units.  With n >= 128 rows and the tensor-core
+ * backend (the default) the forward products run as tcgen05.mma (BF16 x BF16,
+ * FP32 accumulator in tensor memory); a tensor-core wait that gives up
+ * returns DPD_ERR_TIMEOUT. */
 int sur_predict(sur_ctx *s, const float *X, int n, float *Y, float *spread);
+
+/* Forward products of prediction on tcgen05 (1, default) or on warp-level
+ * mma.sync (0); training always uses the latter. */
+int sur_set_backend(sur_ctx *s, int use_tcgen05);
+
+/* Device time of `reps` forward passes of every member over the first n rows
+ * of the inputs the last sur_predict uploaded (inputs stay resident; no host
+ * copies), between CUDA events; ms_per_pass: per pass of all members. */
+int sur_bench_forward(sur_ctx *s, int n, int reps, double *ms_per_pass);
 
 #ifdef __cplusplus
 }

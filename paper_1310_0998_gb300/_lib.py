@@ -117,6 +117,8 @@ def _declare(L):
         "sur_gradients": ([vp, c_int, vp, vp, c_int, P(ctypes.c_float), vp, vp, vp, vp, vp, vp], c_int),
         "sur_train": ([vp, vp, vp, c_int, c_int, c_int, ctypes.c_float, P(ctypes.c_float)], c_int),
         "sur_predict": ([vp, vp, c_int, vp, vp], c_int),
+        "sur_set_backend": ([vp, c_int], c_int),
+        "sur_bench_forward": ([vp, c_int, c_int, P(d)], c_int),
     }
     for name, (args, res) in sig.items():
         if hasattr(L, name):

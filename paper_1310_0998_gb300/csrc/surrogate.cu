@@ -17,6 +17,7 @@
 //   gate         dZ = dA * silu'(Z), stored as BF16 and transposed
 // Padding: K and N are multiples of 16; padded input columns and output rows
 // are zero and stay zero (zero gradients under Adam).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -227,6 +228,275 @@ __global__ void k_predict_out(const float *__restrict__ Yall, int K, int n, int 
     if (spread) spread[idx] = K > 1 ? sqrtf(fmaxf(s2 / K - mean * mean, 0.f)) : 0.f;
 }
 
+// ---------------------------------------------------------------------------
+// Forward pass on the 5th-generation tensor cores, for batches of 128 rows or
+// more (prediction).  Conventions shared by the pieces below: operands sit in
+// shared memory in the canonical no-swizzle K-major layout (core matrices of
+// 8 rows x 16 bytes; core matrices adjacent in K 128 bytes apart = leading
+// byte offset; 8-row groups (K/8) * 128 bytes apart = stride byte offset);
+// one thread issues tcgen05.mma (kind::f16: BF16 x BF16 -> FP32 in tensor
+// memory, 128 x N x 16 per instruction) and commits to an mbarrier; every
+// thread waits on it a bounded number of times and the CTA takes one common
+// decision on a timeout (flag the error word, wait once more for the MMAs in
+// flight, free the tensor memory, return); tcgen05.ld reads the accumulator
+// back, warp w holding rows 32w..32w+31 (one row per lane).
+constexpr int TC_M = 128;
+constexpr long long TC_SPIN = 1ll << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // bits 46-47: descriptor version 1
+}
+
+// kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A BF16 (7-9 = 1),
+// B BF16 (10-12 = 1), A and B K-major (bits 15, 16 = 0), N/8 at 17-22, M/16 at 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long long i = 0; i < TC_SPIN; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Fused forward pass of one member for 128-row tiles, persistent (one CTA per
+// SM).  The CTA stages W1, W2, W3 once as K-major core matrices (8, 128 and
+// 24 KB) and keeps them in shared memory; per tile the inputs go into the
+// activation buffer (64 KB), layer l runs as tcgen05.mma into tensor memory
+// (256 columns), and the epilogue reads the accumulator back (warp w: rows
+// 32w..32w+31), adds the bias, applies SiLU and writes the BF16 activations
+// into the same buffer in the operand layout of the next layer; only the 48
+// output columns go to global memory.  231,632 bytes of shared memory.
+constexpr int FW_W1 = NH * NIN_P * 2, FW_W2 = NH * NH * 2, FW_W3 = NOUT_P * NH * 2, FW_ACT = TC_M * NH * 2;
+constexpr int FW_BIAS = (NH + NH + NOUT_P) * 4;
+constexpr int FW_SMEM = FW_W1 + FW_W2 + FW_W3 + FW_ACT + FW_BIAS + 16;
+
+// [rows x K] K-contiguous BF16 (leading dimension ld) -> K-major core
+// matrices: 16-byte chunk (r, c) at ((r/8) (K/8) + c) 128 + (r%8) 16.
+__device__ __forceinline__ void stage_kmajor(unsigned char *dst, const __nv_bfloat16 *src, int rows, int K, int ld)
+{
+    const int ncm = K >> 3;
+    for (int q = threadIdx.x; q < rows * ncm; q += blockDim.x) {
+        const int r = q / ncm, c = q - r * ncm;
+        const uint4 v = *reinterpret_cast<const uint4 *>(src + (size_t)r * ld + 8 * c);
+        *reinterpret_cast<uint4 *>(dst + ((r >> 3) * ncm + c) * 128 + (r & 7) * 16) = v;
+    }
+}
+
+// One layer's products, issued by a single thread: D[128 x N] = A[128 x K] B[N x K]^T.
+__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, int K, int N, uint32_t mbar)
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t idesc = tc_idesc(TC_M, N), sbo = (uint32_t)(K >> 3) * 128u;
+    for (int ks = 0; ks < (K >> 4); ++ks) {
+        const uint64_t ad = tc_desc(a + ks * 256, 128, sbo), bd = tc_desc(b + ks * 256, 128, sbo);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+// tcgen05.ld of 16 columns of this warp's lane quadrant; the registers are
+// valid only after tmem_wait, which takes them as operands so that no use can
+// be scheduled before it.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t addr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                 " [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(addr));
+}
+
+// 32 columns of this warp's lane quadrant in one load (the CTA has registers
+// to spare: one 256-thread CTA per SM)
+__device__ __forceinline__ void tmem_ld32_sync(uint32_t addr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(addr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait(uint32_t *r)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :: "memory");
+}
+
+// SiLU for the tensor-core epilogue, which is bound by this arithmetic:
+// silu(z) = z sigmoid(z) = z/2 (1 + tanh(z/2)), one tanh.approx.f32 (a single
+// special-function operation, relative error about 2^-11, below the BF16
+// rounding that follows) instead of an exponential and a reciprocal.
+__device__ __forceinline__ float silu_fast(float z)
+{
+    const float h = 0.5f * z;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+    return fmaf(h, t, h);
+}
+
+// Accumulator + bias -> SiLU -> BF16 activations in the K = 256 operand layout
+// of the next layer.  8 warps: warp w reads the rows of lane quadrant w % 4
+// (tcgen05.ld reaches only its own quadrant) and the column half w / 4.
+__device__ __forceinline__ void epi_silu(uint32_t tmem, const float *bias, unsigned char *act)
+{
+    const int warp = threadIdx.x >> 5, q = warp & 3, half = warp >> 2;
+    const int r = 32 * q + (threadIdx.x & 31);
+    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
+    const int cb = half * (NH / 2), ce = cb + NH / 2;
+    unsigned char *row = act + (r & 7) * 16 + (r >> 3) * (NH / 8) * 128;
+#pragma unroll 1
+    for (int c0 = cb; c0 < ce; c0 += 32) {
+        uint32_t u[32];
+        tmem_ld32_sync(tb + (uint32_t)c0, u);
+        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
+        uint32_t h[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 b = b4[j];
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j]) + b.x),
+                                                            silu_fast(__uint_as_float(u[4 * j + 1]) + b.y));
+            const __nv_bfloat162 p1 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j + 2]) + b.z),
+                                                            silu_fast(__uint_as_float(u[4 * j + 3]) + b.w));
+            h[2 * j] = *reinterpret_cast<const uint32_t *>(&p0);
+            h[2 * j + 1] = *reinterpret_cast<const uint32_t *>(&p1);
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            *reinterpret_cast<uint4 *>(row + ((c0 >> 3) + g) * 128) =
+                make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+    }
+}
+
+constexpr int FW_THREADS = 256;
+
+__global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ X0,
+                                                       const __nv_bfloat16 *__restrict__ W1,
+                                                       const __nv_bfloat16 *__restrict__ W2,
+                                                       const __nv_bfloat16 *__restrict__ W3,
+                                                       const float *__restrict__ b1, const float *__restrict__ b2,
+                                                       const float *__restrict__ b3, float *__restrict__ Y,
+                                                       int ntiles, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sW1 = sm, *sW2 = sm + FW_W1, *sW3 = sW2 + FW_W2, *sAct = sW3 + FW_W3;
+    float *sb = reinterpret_cast<float *>(sAct + FW_ACT);   // b1[256], b2[256], b3[48]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + NH + NH + NOUT_P);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t mb = smem_u32(mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+    stage_kmajor(sW1, W1, NH, NIN_P, NIN_P);
+    stage_kmajor(sW2, W2, NH, NH, NH);
+    stage_kmajor(sW3, W3, NOUT_P, NH, NH);
+    for (int i = tid; i < NH + NH + NOUT_P; i += blockDim.x)
+        sb[i] = i < NH ? b1[i] : (i < 2 * NH ? b2[i - NH] : b3[i - 2 * NH]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t aA = smem_u32(sAct), a1 = smem_u32(sW1), a2 = smem_u32(sW2), a3 = smem_u32(sW3);
+    uint32_t parity = 0;
+    bool ok = true;
+    // the 128 x 16 input block of a tile is 256 chunks of 16 bytes, one per
+    // thread: chunk (row tid / 2, column half tid % 2); the next tile's chunk is
+    // loaded into registers while the current tile runs its three layers
+    static_assert(FW_THREADS == TC_M * (NIN_P / 8), "one 16-byte input chunk per thread");
+    const int xr = tid >> 1, xc = tid & 1;
+    const int xoff = ((xr >> 3) * 2 + xc) * 128 + (xr & 7) * 16;
+    uint4 xcur = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x < ntiles)
+        xcur = *reinterpret_cast<const uint4 *>(X0 + (size_t)(blockIdx.x * TC_M + xr) * NIN_P + 8 * xc);
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int m0 = tile * TC_M;
+        *reinterpret_cast<uint4 *>(sAct + xoff) = xcur;
+        uint4 xnext = make_uint4(0u, 0u, 0u, 0u);
+        if (tile + (int)gridDim.x < ntiles)
+            xnext = *reinterpret_cast<const uint4 *>(X0 + (size_t)((tile + gridDim.x) * TC_M + xr) * NIN_P + 8 * xc);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+#pragma unroll 1
+        for (int layer = 0; layer < 3; ++layer) {
+            if (tid == 0) {
+                if (layer == 0) mma_layer(tmem, aA, a1, NIN_P, NH, mb);
+                else if (layer == 1) mma_layer(tmem, aA, a2, NH, NH, mb);
+                else mma_layer(tmem, aA, a3, NH, NOUT_P, mb);
+            }
+            // one decision for the whole CTA (barriers follow)
+            if (__syncthreads_or(tc_wait(mb, parity) ? 0 : 1)) {
+                ok = false;
+                if (tid == 0) atomicOr(err, 1);
+                tc_wait(mb, parity);   // second bounded wait for MMAs still in flight
+                break;
+            }
+            parity ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (layer < 2) {
+                epi_silu(tmem, sb + layer * NH, sAct);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            } else {
+                // 48 output columns: chunks 0, 1 by the first column half, chunk 2 by the second
+                const int q = warp & 3, half = warp >> 2;
+                const int row = m0 + 32 * q + lane;
+                const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+                for (int c0 = half ? 32 : 0; c0 < (half ? NOUT_P : 32); c0 += 16) {
+                    uint32_t u[16];
+                    tmem_ld16_issue(tb + (uint32_t)c0, u);
+                    tmem_wait(u);
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(u[j]);
+                    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)row * NOUT_P + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        dst[j] = make_float4(v[4 * j] + sb[2 * NH + c0 + 4 * j], v[4 * j + 1] + sb[2 * NH + c0 + 4 * j + 1],
+                                             v[4 * j + 2] + sb[2 * NH + c0 + 4 * j + 2],
+                                             v[4 * j + 3] + sb[2 * NH + c0 + 4 * j + 3]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();   // accumulator and activation buffer free for the next layer / tile
+        }
+        xcur = xnext;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
+}
+
 struct Member {
     float *w[3], *b[3];                 // FP32 masters
     float *mw[3], *vw[3], *mb[3], *vb[3];
@@ -251,6 +521,8 @@ struct sur_ctx {
     float *Z1, *Z2, *Y, *dA, *dY32, *T, *Xin, *loss, *Yall, *Yout, *Sout;
     int64_t adam_t = 0;
     float *h_loss = nullptr;
+    int *d_err = nullptr;   // bounded-wait timeouts of the tensor-core GEMM
+    int tc = 1;             // forward passes of >= 128 rows on tcgen05 (0: mma.sync)
 };
 
 static const int DIMS_IN[3] = {NIN_P, NH, NH};
@@ -277,6 +549,26 @@ static void forward(sur_ctx *s, int k, int M, float *Yout)
     gemm(s, s->X0, m.wbf[0], M, NH, NIN_P, EPI_BIAS_SILU, m.b[0], nullptr, s->Z1, s->A1, s->A1T);
     gemm(s, s->A1, m.wbf[1], M, NH, NH, EPI_BIAS_SILU, m.b[1], nullptr, s->Z2, s->A2, s->A2T);
     gemm(s, s->A2, m.wbf[2], M, NOUT_P, NH, EPI_BIAS, m.b[2], nullptr, Yout, nullptr, nullptr);
+}
+
+// Forward pass of member k on the tensor cores (M a multiple of 128): the
+// fused persistent kernel, one CTA per SM at most.
+static void forward_fused(sur_ctx *s, int k, int M, float *Yout)
+{
+    static bool attr = false;
+    static int nsm = 0;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        attr = true;
+    }
+    Member &m = s->mem[k];
+    const int ntiles = M / TC_M;
+    const int grid = std::min(ntiles, std::max(nsm, 1));
+    k_mlp_fwd_tc<<<grid, FW_THREADS, FW_SMEM, s->st>>>(s->X0, m.wbf[0], m.wbf[1], m.wbf[2], m.b[0], m.b[1], m.b[2], Yout,
+                                                ntiles, s->d_err);
 }
 
 // Loss and gradients of member k for n valid rows (M padded rows).
@@ -358,7 +650,7 @@ int sur_create(int n_members, int max_rows, uint64_t seed, void *stream, sur_ctx
     sur_ctx *s = new (std::nothrow) sur_ctx();
     if (!s) return DPD_ERR_OOM;
     s->K = n_members;
-    s->cap = (max_rows + 63) & ~63;
+    s->cap = (max_rows + 127) & ~127;
     if (stream) s->st = (cudaStream_t)stream;
     else {
         if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) { delete s; return DPD_ERR_CUDA; }
@@ -386,7 +678,7 @@ int sur_create(int n_members, int max_rows, uint64_t seed, void *stream, sur_ctx
                  o_Z1 = take(4 * M * NH), o_Z2 = take(4 * M * NH), o_Y = take(4 * M * NOUT_P),
                  o_dA = take(4 * M * NH), o_dY32 = take(4 * M * NOUT_P), o_T = take(4 * M * NOUT),
                  o_Xin = take(4 * M * NIN), o_loss = take(64), o_Yall = take(4 * M * NOUT_P * (size_t)s->K),
-                 o_Yout = take(4 * M * NOUT), o_Sout = take(4 * M * NOUT);
+                 o_Yout = take(4 * M * NOUT), o_Sout = take(4 * M * NOUT), o_err = take(4);
     if (cudaMalloc(&s->pool, off) != cudaSuccess || cudaMallocHost((void **)&s->h_loss, 64) != cudaSuccess) {
         sur_destroy(s);
         return DPD_ERR_OOM;
@@ -414,6 +706,7 @@ int sur_create(int n_members, int max_rows, uint64_t seed, void *stream, sur_ctx
     s->dY32 = (float *)(p + o_dY32); s->T = (float *)(p + o_T); s->Xin = (float *)(p + o_Xin);
     s->loss = (float *)(p + o_loss); s->Yall = (float *)(p + o_Yall); s->Yout = (float *)(p + o_Yout);
     s->Sout = (float *)(p + o_Sout);
+    s->d_err = (int *)(p + o_err);
     // identity standardisation until training sets it
     std::vector<float> ones(256, 1.f);
     cudaMemcpyAsync(s->sd_x, ones.data(), 4 * 64, cudaMemcpyHostToDevice, s->st);
@@ -576,19 +869,59 @@ int sur_train(sur_ctx *s, const float *X, const float *Y, int n, int epochs, int
     return DPD_OK;
 }
 
+int sur_bench_forward(sur_ctx *s, int n, int reps, double *ms_per_pass)
+{
+    if (!s || !ms_per_pass || n < 1 || n > s->cap || reps < 1) return DPD_ERR_INVALID_ARG;
+    const bool tc = s->tc && n >= TC_M;
+    const int M = tc ? (n + TC_M - 1) / TC_M * TC_M : (n + 63) & ~63;
+    cudaEvent_t e0, e1;
+    CUS(cudaEventCreate(&e0));
+    CUS(cudaEventCreate(&e1));
+    if (tc) CUS(cudaMemsetAsync(s->d_err, 0, 4, s->st));
+    CUS(cudaEventRecord(e0, s->st));
+    for (int r = 0; r < reps; ++r)
+        for (int k = 0; k < s->K; ++k) {
+            if (tc) forward_fused(s, k, M, s->Yall + (size_t)k * M * NOUT_P);
+            else forward(s, k, M, s->Yall + (size_t)k * M * NOUT_P);
+        }
+    CUS(cudaEventRecord(e1, s->st));
+    CUS(cudaGetLastError());
+    CUS(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_pass = ms / reps;
+    return DPD_OK;
+}
+
+int sur_set_backend(sur_ctx *s, int use_tcgen05)
+{
+    if (!s || (use_tcgen05 != 0 && use_tcgen05 != 1)) return DPD_ERR_INVALID_ARG;
+    s->tc = use_tcgen05;
+    return DPD_OK;
+}
+
 int sur_predict(sur_ctx *s, const float *X, int n, float *Y, float *spread)
 {
     if (!s || !X || !Y || n < 1 || n > s->cap) return DPD_ERR_INVALID_ARG;
-    const int M = (n + 63) & ~63;
+    const bool tc = s->tc && n >= TC_M;
+    const int M = tc ? (n + TC_M - 1) / TC_M * TC_M : (n + 63) & ~63;
     int rc = upload_inputs(s, X, n, M);
     if (rc) return rc;
-    for (int k = 0; k < s->K; ++k) forward(s, k, M, s->Yall + (size_t)k * M * NOUT_P);
+    if (tc) CUS(cudaMemsetAsync(s->d_err, 0, 4, s->st));
+    for (int k = 0; k < s->K; ++k) {
+        if (tc) forward_fused(s, k, M, s->Yall + (size_t)k * M * NOUT_P);
+        else forward(s, k, M, s->Yall + (size_t)k * M * NOUT_P);
+    }
     k_predict_out<<<(n * NOUT + 255) / 256, 256, 0, s->st>>>(s->Yall, s->K, n, M, s->mu_y, s->sd_y, s->Yout,
                                                             spread ? s->Sout : nullptr);
     CUS(cudaGetLastError());
     CUS(cudaMemcpyAsync(Y, s->Yout, 4 * (size_t)n * NOUT, cudaMemcpyDeviceToHost, s->st));
     if (spread) CUS(cudaMemcpyAsync(spread, s->Sout, 4 * (size_t)n * NOUT, cudaMemcpyDeviceToHost, s->st));
+    if (tc) CUS(cudaMemcpyAsync(s->h_loss + 8, s->d_err, 4, cudaMemcpyDeviceToHost, s->st));
     CUS(cudaStreamSynchronize(s->st));
+    if (tc && *reinterpret_cast<int *>(s->h_loss + 8)) return DPD_ERR_TIMEOUT;
     return DPD_OK;
 }
 

@@ -152,6 +152,17 @@ class Surrogate:
         check(self._lib.sur_predict(self._h, _lib.ptr(X), X.shape[0], _lib.ptr(Y), _lib.ptr(S)), "sur_predict")
         return Y, S
 
+    def set_backend(self, tcgen05: bool):
+        """Forward products of prediction (>= 128 rows) on tcgen05 or mma.sync."""
+        check(self._lib.sur_set_backend(self._h, 1 if tcgen05 else 0), "sur_set_backend")
+
+    def bench_forward(self, n: int, reps: int = 20) -> float:
+        """Device ms per forward pass of all members over the last n predicted
+        rows (no host copies)."""
+        ms = ctypes.c_double()
+        check(self._lib.sur_bench_forward(self._h, int(n), int(reps), ctypes.byref(ms)), "sur_bench_forward")
+        return ms.value
+
     def gradients(self, member, X, Y):
         X = np.ascontiguousarray(X, np.float32)
         Y = np.ascontiguousarray(Y, np.float32)

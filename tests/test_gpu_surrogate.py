@@ -136,6 +136,33 @@ def test_predict_matches_oracle_members(sur):
     assert np.max(np.abs(S - spread)) <= 2e-3 * scale
 
 
+@pytest.mark.parametrize("n", [128, 300, 4096])
+def test_tensor_core_prediction(n):
+    """Prediction with the tcgen05 forward products (n >= 128 rows, ragged
+    tails included) against the mma.sync products and the FP64 oracle."""
+    from paper_1310_0998_gb300.surrogate import Surrogate
+    s = Surrogate(members=2, max_rows=4096, seed=9)
+    try:
+        ps = [_params32(61), _params32(62)]
+        for k, p in enumerate(ps):
+            s.set_weights(k, p)
+        mu_x, sd_x, mu_y, sd_y = _scaling(63)
+        s.set_scaling(mu_x, sd_x, mu_y, sd_y)
+        X = _rows(n, 64)
+        s.set_backend(True)
+        Yt, St = s.predict(X)
+        s.set_backend(False)
+        Ym, Sm = s.predict(X)
+    finally:
+        s.close()
+    scale = np.abs(Ym).max() + 1.0
+    assert np.max(np.abs(Yt - Ym)) <= 2e-3 * scale
+    assert np.max(np.abs(St - Sm)) <= 2e-3 * scale
+    x = _std_inputs(X, mu_x, sd_x)
+    ys = np.stack([mlp.forward([a.astype(np.float64) for a in p], x)["y"][:, :40] * sd_y + mu_y for p in ps])
+    assert np.max(np.abs(Yt - ys.mean(axis=0))) <= 2e-3 * scale
+
+
 def test_training_fits_and_spread_grows_off_range():
     from paper_1310_0998_gb300.surrogate import Surrogate
     s = Surrogate(members=4, max_rows=1024, seed=3)
