@@ -18,7 +18,9 @@
 //   C_p, C_v, C_f   canonical (X_s, v_s, f_s) in id order after each call
 // One step: scan, scatter, then one thread per bead walks the full 3x3x3
 // stencil (every pair is evaluated from both sides with the same random
-// number, so the forces are antisymmetric bit for bit), adds bond,
+// number, so each pair force is antisymmetric bit for bit; the pairs inside
+// r_c go through a warp queue so that their arithmetic runs on full warps),
+// adds bond,
 // propulsion and drag, does the second half-kick, the FP64 thermo partials,
 // the next half-kick and drift, and bins the new position.
 #include <cmath>
@@ -117,53 +119,119 @@ __device__ __forceinline__ float pair_scalar3(const Sys &d, float r2, float rinv
     return d.a * w - d.gamma * (wr * wr) * dve + d.sig_r * wr * nz;
 }
 
-__global__ void __launch_bounds__(256) k3_force(Sys3 s, int flags)
+// One queued pair (sorted slot q, owner lane o of this warp): the pair force
+// on the owner, accumulated in shared memory.
+__device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const uint4 *pis, const float4 *vis,
+                                      float (*fs)[4], uint32_t s_lo, uint32_t s_hi)
+{
+    const Sys &d = s.b;
+    const uint4 pi = pis[o], pj = s.S_p[q];
+    const float4 vi = vis[o], vj = s.S_v[q];
+    const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rinv = rsqrtf(r2);
+    const float ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;   // e = (x_i - x_j)/r
+    const float dve = (vi.x - vj.x) * ex + (vi.y - vj.y) * ey + (vi.z - vj.z) * ez;
+    const float F = pair_scalar3(d, r2, rinv, dve, pi.w, pj.w, s_lo, s_hi);
+    atomicAdd(&fs[o][0], F * ex);
+    atomicAdd(&fs[o][1], F * ey);
+    atomicAdd(&fs[o][2], F * ez);
+}
+
+// Thread per bead over the full 3x3x3 stencil.  The lanes of a warp test their
+// candidates in step (one per lane per iteration, as many iterations as the
+// longest cell range in the warp) and push the pairs inside r_c, as (slot,
+// owner lane), into the warp's queue; every 32 queued pairs the whole warp
+// evaluates Philox and the force together, so that arithmetic runs with every
+// lane busy whatever the neighbour counts.
+__global__ void __launch_bounds__(256, 5) k3_force(Sys3 s, int flags)
 {
     const Sys &d = s.b;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    __shared__ uint32_t s_q[8][64];
+    __shared__ unsigned char s_ql[8][64];
+    __shared__ uint4 s_pi[8][32];
+    __shared__ float4 s_vi[8][32];
+    __shared__ float s_f[8][32][4];
     float ke = 0.f, px = 0.f, py = 0.f, pz = 0.f;
-    if (g < d.n) {
-        const long long step = *d.step;
-        const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
-        const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
-        const uint4 pi = s.S_p[g];
-        const float4 vi = s.S_v[g];
-        const uint32_t id = pi.w, pid = d.excl ? (id ^ 1u) : 0xffffffffu;
-        const uint32_t n = (uint32_t)d.n;
-        const int cx = cell_coord(d, pi.x), cy = cell_coord(d, pi.y), cz = cell_coord(d, pi.z);
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int oz = -1; oz <= 1; ++oz) {
-            int z = cz + oz;
-            z += z < 0 ? d.nc : (z >= d.nc ? -d.nc : 0);
-            for (int oy = -1; oy <= 1; ++oy) {
-                int y = cy + oy;
-                y += y < 0 ? d.nc : (y >= d.nc ? -d.nc : 0);
-                const int row = (z * d.nc + y) * d.nc;
-                for (int ox = -1; ox <= 1; ++ox) {
-                    int x = cx + ox;
-                    x += x < 0 ? d.nc : (x >= d.nc ? -d.nc : 0);
+    const bool active = g < d.n;
+    const long long step = *d.step;
+    const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
+    const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+    const uint32_t n = (uint32_t)d.n;
+    const uint4 pi = active ? s.S_p[g] : make_uint4(0u, 0u, 0u, 0xffffffffu);
+    const float4 vi = active ? s.S_v[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t id = pi.w, pid = d.excl ? (id ^ 1u) : 0xffffffffu;
+    s_pi[warp][lane] = pi;
+    s_vi[warp][lane] = vi;
+    s_f[warp][lane][0] = 0.f;
+    s_f[warp][lane][1] = 0.f;
+    s_f[warp][lane][2] = 0.f;
+    __syncwarp();
+    const int cx = cell_coord(d, pi.x), cy = cell_coord(d, pi.y), cz = cell_coord(d, pi.z);
+    int qn = 0;
+    for (int oz = -1; oz <= 1; ++oz) {
+        int z = cz + oz;
+        z += z < 0 ? d.nc : (z >= d.nc ? -d.nc : 0);
+        for (int oy = -1; oy <= 1; ++oy) {
+            int y = cy + oy;
+            y += y < 0 ? d.nc : (y >= d.nc ? -d.nc : 0);
+            const int row = (z * d.nc + y) * d.nc;
+            for (int ox = -1; ox <= 1; ++ox) {
+                int x = cx + ox;
+                x += x < 0 ? d.nc : (x >= d.nc ? -d.nc : 0);
+                uint32_t b = 0, e = 0;
+                if (active) {
                     const int c = row + x;
-                    const uint32_t b = min(d.cstart[c], n), e = min(max(d.cstart[c + 1], b), n);
-                    for (uint32_t q = b; q < e; ++q) {
-                        if (q == (uint32_t)g) continue;
+                    b = min(d.cstart[c], n);
+                    e = min(max(d.cstart[c + 1], b), n);
+                }
+                const int len = (int)(e - b);
+                const int maxlen = __reduce_max_sync(FULL, len);
+                for (int t = 0; t < maxlen; ++t) {
+                    const uint32_t q = b + (uint32_t)t;
+                    bool hit = false;
+                    if (t < len && q != (uint32_t)g) {
                         const uint4 pj = s.S_p[q];
-                        if (pj.w == pid) continue;
-                        const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < d.rc2 && r2 > 0.f) {
-                            const float4 vj = s.S_v[q];
-                            const float rinv = rsqrtf(r2);
-                            const float ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;   // e = (x_i - x_j)/r
-                            const float dve = (vi.x - vj.x) * ex + (vi.y - vj.y) * ey + (vi.z - vj.z) * ez;
-                            const float F = pair_scalar3(d, r2, rinv, dve, id, pj.w, s_lo, s_hi);
-                            fx += F * ex;
-                            fy += F * ey;
-                            fz += F * ez;
+                        if (pj.w != pid) {
+                            const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y),
+                                        dz = mdiff(d, pi.z, pj.z);
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            hit = (r2 < d.rc2) & (r2 > 0.f);
                         }
+                    }
+                    const unsigned m = __ballot_sync(FULL, hit);
+                    if (hit) {
+                        const int pos = qn + __popc(m & lt);
+                        s_q[warp][pos] = q;
+                        s_ql[warp][pos] = (unsigned char)lane;
+                    }
+                    qn += __popc(m);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        const uint32_t mq = s_q[warp][lane];
+                        const int mo = s_ql[warp][lane];
+                        const uint32_t cq = s_q[warp][32 + lane];
+                        const unsigned char co = s_ql[warp][32 + lane];
+                        __syncwarp();
+                        if (lane < qn - 32) {
+                            s_q[warp][lane] = cq;
+                            s_ql[warp][lane] = co;
+                        }
+                        qn -= 32;
+                        eval3(s, mq, mo, s_pi[warp], s_vi[warp], s_f[warp], s_lo, s_hi);
+                        __syncwarp();
                     }
                 }
             }
         }
+    }
+    if (lane < qn) eval3(s, s_q[warp][lane], s_ql[warp][lane], s_pi[warp], s_vi[warp], s_f[warp], s_lo, s_hi);
+    __syncwarp();
+    if (active) {
+        float fx = s_f[warp][lane][0], fy = s_f[warp][lane][1], fz = s_f[warp][lane][2];
         // bond and propulsion (partner id ^ 1), drag on the half-step velocity
         const uint32_t ps = s.slot[id ^ 1u];
         if (ps < n) {
