@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
         // look-back scan (the chunk comes from the replica's ticket)
         for (int it = blockIdx.x; it < n_scan; it += nb) {
             const Sys &d = sys[scan_items[it]];
-            scan_decoupled_t<TILE_THREADS>(d, (d.ncells + SCAN_TILE - 1) / SCAN_TILE);
+            scan_decoupled_t<TILE_THREADS>(d, (d.ncells + SCAN_TILE - 1) / SCAN_TILE, (uint32_t *)smem);
         }
         grid_barrier(bar, nb, berr, 0);
         // phase 2: scatter U -> S in chunks of ENS_CHUNK beads
@@ -219,7 +219,8 @@ static int ens_build_tables(dpd_batch *b)
     for (int r = 0; r < b->R; ++r) sys[r].cap = cap;
     for (int r = 0; r < b->R; ++r) b->reps[r]->d.cap = cap;
     b->cap = cap;
-    b->smem = force_smem(b->B, b->var, cap, false);
+    // the dynamic buffer also serves the scan phase's transpose
+    b->smem = std::max(force_smem(b->B, b->var, cap, false), sizeof(uint32_t) * (size_t)SCAN_BUF);
     b->n_scan = (int)scan.size();
     b->n_scat = (int)scat.size();
     b->n_tiles = (int)tiles.size();

@@ -18,7 +18,11 @@
 namespace dpd {
 
 // ----------------------------------------------------------------- kernels ----
-__global__ void __launch_bounds__(SCAN_NT) k_scan(Sys d, int nblocks) { scan_decoupled(d, nblocks); }
+__global__ void __launch_bounds__(SCAN_NT) k_scan(Sys d, int nblocks)
+{
+    __shared__ uint32_t s_buf[SCAN_BUF];
+    scan_decoupled_t<SCAN_NT>(d, nblocks, s_buf);
+}
 
 template <int B>
 __global__ void k_scatter(Sys d)

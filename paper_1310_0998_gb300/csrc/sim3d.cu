@@ -45,7 +45,11 @@ __device__ __forceinline__ int cell3(const Sys &d, uint32_t X, uint32_t Y, uint3
     return (cell_coord(d, Z) * d.nc + cell_coord(d, Y)) * d.nc + cell_coord(d, X);
 }
 
-__global__ void k3_scan(Sys d, int nblocks) { scan_decoupled(d, nblocks); }
+__global__ void __launch_bounds__(SCAN_NT) k3_scan(Sys d, int nblocks)
+{
+    __shared__ uint32_t s_buf[SCAN_BUF];
+    scan_decoupled_t<SCAN_NT>(d, nblocks, s_buf);
+}
 
 __global__ void k3_bin(Sys3 s)
 {

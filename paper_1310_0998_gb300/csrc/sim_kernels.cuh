@@ -21,14 +21,21 @@ namespace dpd {
 // ticket so predecessors always run first; the epoch (ticket / nblocks) tags
 // the status words so nothing needs clearing between launches.  Waits are
 // bounded: on timeout the error bit is set and the scan continues.  NT
-// threads per block, SCAN_TILE / NT cells each: every block size cuts the
-// cells into the same SCAN_TILE chunks, so the ticket epochs of a context
-// stay consistent whichever kernel scans it.
+// threads per block: every block size cuts the cells into the same SCAN_TILE
+// chunks, so the ticket epochs of a context stay consistent whichever kernel
+// scans it.  Counts are read (and zeroed) and cell starts written with
+// consecutive lanes on consecutive cells; the shared buffer s_buf
+// (SCAN_BUF words, one pad word per 32 so that a thread's run of consecutive
+// cells sits in distinct banks) turns that order into runs of SCAN_TILE / NT
+// cells per thread and back.
+constexpr int SCAN_BUF = SCAN_TILE + SCAN_TILE / 32;
+__device__ __forceinline__ int scan_pad(int e) { return e + (e >> 5); }
+
 template <int NT>
-__device__ inline void scan_decoupled_t(const Sys &d, int nblocks)
+__device__ inline void scan_decoupled_t(const Sys &d, int nblocks, uint32_t *s_buf)
 {
-    constexpr int SCAN_IPT = SCAN_TILE / NT;
-    static_assert(SCAN_IPT * NT == SCAN_TILE && NT % 32 == 0 && NT <= 1024, "scan block shape");
+    constexpr int IPT = SCAN_TILE / NT;
+    static_assert(IPT * NT == SCAN_TILE && NT % 32 == 0 && NT <= 1024, "scan block shape");
     __shared__ uint32_t s_warp[NT / 32];
     __shared__ uint32_t s_excl;
     __shared__ int s_bid;
@@ -42,26 +49,29 @@ __device__ inline void scan_decoupled_t(const Sys &d, int nblocks)
     __syncthreads();
     const int bid = s_bid;
     const unsigned long long ep = s_epoch;
-    const int base = bid * SCAN_TILE + tid * SCAN_IPT;
-    // up to 16 counts per thread stay in registers; more (narrow blocks, as in
-    // the persistent ensemble kernel) are read again from L2 after the scan
-    constexpr bool KEEP = SCAN_IPT <= 16;
-    uint32_t v[KEEP ? SCAN_IPT : 1];
-    uint32_t sum = 0;
+    const int base = bid * SCAN_TILE;
+    // batches of eight loads in flight, then the zeroing stores
+    static_assert(IPT % 8 == 0, "scan load batches");
 #pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        const int idx = base + k;
-        const uint32_t c = idx < d.ncells ? d.counts[idx] : 0u;
-        if constexpr (KEEP) v[k] = c;
-        sum += c;
-    }
-    if constexpr (KEEP) {
+    for (int k0 = 0; k0 < IPT; k0 += 8) {
+        uint32_t c[8];
 #pragma unroll
-        for (int k = 0; k < SCAN_IPT; ++k) {
-            const int idx = base + k;
-            if (idx < d.ncells) d.counts[idx] = 0u;
+        for (int k = 0; k < 8; ++k) {
+            const int idx = base + (k0 + k) * NT + tid;
+            c[k] = idx < d.ncells ? d.counts[idx] : 0u;
         }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s_buf[scan_pad((k0 + k) * NT + tid)] = c[k];
     }
+#pragma unroll 8
+    for (int k = 0; k < IPT; ++k) {
+        const int idx = base + k * NT + tid;
+        if (idx < d.ncells) d.counts[idx] = 0u;
+    }
+    __syncthreads();
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int k = 0; k < IPT; ++k) sum += s_buf[scan_pad(tid * IPT + k)];
     // block exclusive scan of the per-thread sums
     const int lane = tid & 31, wid = tid >> 5;
     uint32_t incl = sum;
@@ -81,48 +91,64 @@ __device__ inline void scan_decoupled_t(const Sys &d, int nblocks)
             if (lane >= o) wi += t;
         }
         if (lane < NT / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
-        if (lane == NT / 32 - 1) {
-            const uint32_t total = wi;
-            uint32_t excl = 0;
-            unsigned long long *st = d.scan_status;
-            if (bid == 0) {
-                st_release_u64(&st[0], (ep << 34) | (2ull << 32) | total);
-            } else {
-                st_release_u64(&st[bid], (ep << 34) | (1ull << 32) | total);
-                int j = bid - 1;
-                long long spins = 0;
-                while (j >= 0) {
-                    const unsigned long long w64 = ld_acquire_u64(&st[j]);
-                    const unsigned long long wep = w64 >> 34, fl = (w64 >> 32) & 3ull;
-                    if (wep != ep || fl == 0ull) {
-                        if (++spins > SPIN_LIMIT) { set_err_at(d, ERR_TIMEOUT, 3, bid, j, 0); break; }
-                        __nanosleep(32);
-                        continue;
-                    }
-                    excl += (uint32_t)w64;
-                    if (fl == 2ull) break;
-                    --j;
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, NT / 32 - 1);
+        uint32_t excl = 0;
+        unsigned long long *st = d.scan_status;
+        if (bid == 0) {
+            if (lane == 0) st_release_u64(&st[0], (ep << 34) | (2ull << 32) | total);
+        } else {
+            if (lane == 0) st_release_u64(&st[bid], (ep << 34) | (1ull << 32) | total);
+            // Warp-wide look-back: lane l reads predecessor top - l.  The
+            // window's words up to the nearest inclusive prefix are added
+            // once all of them are published (aggregate or inclusive); a
+            // window of 32 aggregates is added whole and the window moves
+            // back.  A block therefore needs an inclusive prefix from one
+            // of its 32 nearest predecessors, not from the next one, which
+            // keeps the chain of waits across blocks short.
+            int top = bid - 1;
+            long long spins = 0;
+            while (true) {
+                const int j = top - lane;
+                const unsigned long long w64 = j >= 0 ? ld_acquire_u64(&st[j]) : (2ull << 32);
+                const unsigned long long fl = (w64 >> 32) & 3ull;
+                const bool ok = j < 0 || ((w64 >> 34) == ep && fl != 0ull);
+                const unsigned okm = __ballot_sync(0xffffffffu, ok);
+                const unsigned incm = __ballot_sync(0xffffffffu, ok && fl == 2ull);
+                const int m = incm ? __ffs(incm) - 1 : 31;          // last lane to add
+                const unsigned need = m == 31 ? 0xffffffffu : ((2u << m) - 1u);
+                if ((okm & need) == need) {
+                    excl += __reduce_add_sync(0xffffffffu, (lane <= m && j >= 0) ? (uint32_t)w64 : 0u);
+                    if (incm) break;
+                    top -= 32;
+                    continue;
                 }
-                st_release_u64(&st[bid], (ep << 34) | (2ull << 32) | (excl + total));
+                if (++spins > SPIN_LIMIT) {
+                    if (lane == 0) set_err_at(d, ERR_TIMEOUT, 3, bid, top, 0);
+                    break;
+                }
+                __nanosleep(32);
             }
+            if (lane == 0) st_release_u64(&st[bid], (ep << 34) | (2ull << 32) | (excl + total));
+        }
+        if (lane == 0) {
             s_excl = excl;
             if (bid == nblocks - 1) d.cstart[d.ncells] = excl + total;
         }
     }
     __syncthreads();
     uint32_t run = s_excl + s_warp[wid] + (incl - sum);
-#pragma unroll
-    for (int k = 0; k < SCAN_IPT; ++k) {
-        const int idx = base + k;
-        if constexpr (KEEP) {
-            if (idx < d.ncells) d.cstart[idx] = run;
-            run += v[k];
-        } else if (idx < d.ncells) {
-            const uint32_t c = d.counts[idx];
-            d.counts[idx] = 0u;
-            d.cstart[idx] = run;
-            run += c;
-        }
+#pragma unroll 8
+    for (int k = 0; k < IPT; ++k) {
+        const int i = scan_pad(tid * IPT + k);
+        const uint32_t c = s_buf[i];
+        s_buf[i] = run;
+        run += c;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < IPT; ++k) {
+        const int e = k * NT + tid, idx = base + e;
+        if (idx < d.ncells) d.cstart[idx] = s_buf[scan_pad(e)];
     }
     if (bid == 0 && tid == 0) {
         const long long s1 = *d.step + 1;
@@ -130,9 +156,9 @@ __device__ inline void scan_decoupled_t(const Sys &d, int nblocks)
         double *th = d.thermo + 4 * (size_t)(s1 % THERMO_CAP);
         th[0] = 0.0; th[1] = 0.0; th[2] = 0.0; th[3] = 0.0;
     }
+    __syncthreads();   // s_buf is free again for the caller
 }
 
-__device__ inline void scan_decoupled(const Sys &d, int nblocks) { scan_decoupled_t<SCAN_NT>(d, nblocks); }
 
 // --------------------------------------------------------------- scatter ----
 template <int B>

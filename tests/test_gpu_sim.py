@@ -112,6 +112,22 @@ def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed, variant):
     assert abs(int(tot) - toto) <= int(amb.sum())
 
 
+def test_cell_table_after_many_steps_multiblock_scan(Sim, orc):
+    """L = 512 at density 3: 262,144 cells, 64 scan blocks, so a block's
+    look-back reaches past its 32 nearest predecessors.  After 20, 40 and 60
+    steps the device cell table (from the scan) equals the cell counts of the
+    positions read back (exact multiples of L / 2^32 for this L)."""
+    L, nd = 512.0, 393216
+    x, _ = synth.dimers(nd, L, 0.5, seed=21)
+    with Sim(L, 2 * nd, **sim_kw(seed=21)) as s:
+        s.set_positions(x)
+        nc = s.info().n_cells_side
+        for _ in range(3):
+            s.step(20)
+            xg, _, _, _ = s.get_state()
+            np.testing.assert_array_equal(s.cell_counts(), orc.cell_counts(xg, L, nc))
+
+
 @pytest.mark.parametrize("variant", [2, 3])
 def test_trajectory_parity_c1_100_steps(Sim, orc, variant):
     """C1: 512 dimers, L = 32, seed 0: positions after 100 steps."""
