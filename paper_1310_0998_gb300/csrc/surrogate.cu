@@ -274,8 +274,9 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
 // SM).  The CTA stages W1, W2, W3 once as K-major core matrices (8, 128 and
 // 24 KB) and keeps them in shared memory; per tile the inputs go into the
 // activation buffer (64 KB), layer l runs as tcgen05.mma into tensor memory
-// (256 columns), and the epilogue reads the accumulator back (warp w: rows
-// 32w..32w+31), adds the bias, applies SiLU and writes the BF16 activations
+// (256 columns), and the epilogue reads the accumulator back (16 warps: warp
+// w takes rows 32 (w % 4) .. +31 and a quarter of the columns), adds the
+// bias, applies SiLU and writes the BF16 activations
 // into the same buffer in the operand layout of the next layer; only the 48
 // output columns go to global memory.  231,632 bytes of shared memory.
 constexpr int FW_W1 = NH * NIN_P * 2, FW_W2 = NH * NH * 2, FW_W3 = NOUT_P * NH * 2, FW_ACT = TC_M * NH * 2;
@@ -339,6 +340,30 @@ __device__ __forceinline__ void tmem_ld32_sync(uint32_t addr, uint32_t *r)
                  : "memory");
 }
 
+// 32 columns, issue only: the registers become valid at tmem_wait32
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t addr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void tmem_wait32(uint32_t *r)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :: "memory");
+}
+
 __device__ __forceinline__ void tmem_wait(uint32_t *r)
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -360,40 +385,49 @@ __device__ __forceinline__ float silu_fast(float z)
     return fmaf(h, t, h);
 }
 
-// Accumulator + bias -> SiLU -> BF16 activations in the K = 256 operand layout
-// of the next layer.  8 warps: warp w reads the rows of lane quadrant w % 4
-// (tcgen05.ld reaches only its own quadrant) and the column half w / 4.
-__device__ __forceinline__ void epi_silu(uint32_t tmem, const float *bias, unsigned char *act)
+// 32 accumulator columns (+ bias) -> SiLU -> BF16, stored as four 16-byte
+// chunks of this thread's row in the K-major operand layout.
+__device__ __forceinline__ void silu_store32(const uint32_t *u, const float *bias, unsigned char *row, int c0)
 {
-    const int warp = threadIdx.x >> 5, q = warp & 3, half = warp >> 2;
-    const int r = 32 * q + (threadIdx.x & 31);
-    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
-    const int cb = half * (NH / 2), ce = cb + NH / 2;
-    unsigned char *row = act + (r & 7) * 16 + (r >> 3) * (NH / 8) * 128;
-#pragma unroll 1
-    for (int c0 = cb; c0 < ce; c0 += 32) {
-        uint32_t u[32];
-        tmem_ld32_sync(tb + (uint32_t)c0, u);
-        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
-        uint32_t h[16];
+    const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
+    uint32_t h[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float4 b = b4[j];
-            const __nv_bfloat162 p0 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j]) + b.x),
-                                                            silu_fast(__uint_as_float(u[4 * j + 1]) + b.y));
-            const __nv_bfloat162 p1 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j + 2]) + b.z),
-                                                            silu_fast(__uint_as_float(u[4 * j + 3]) + b.w));
-            h[2 * j] = *reinterpret_cast<const uint32_t *>(&p0);
-            h[2 * j + 1] = *reinterpret_cast<const uint32_t *>(&p1);
-        }
-#pragma unroll
-        for (int g = 0; g < 4; ++g)
-            *reinterpret_cast<uint4 *>(row + ((c0 >> 3) + g) * 128) =
-                make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+    for (int j = 0; j < 8; ++j) {
+        const float4 b = b4[j];
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j]) + b.x),
+                                                        silu_fast(__uint_as_float(u[4 * j + 1]) + b.y));
+        const __nv_bfloat162 p1 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j + 2]) + b.z),
+                                                        silu_fast(__uint_as_float(u[4 * j + 3]) + b.w));
+        h[2 * j] = *reinterpret_cast<const uint32_t *>(&p0);
+        h[2 * j + 1] = *reinterpret_cast<const uint32_t *>(&p1);
     }
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        *reinterpret_cast<uint4 *>(row + ((c0 >> 3) + g) * 128) = make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
 }
 
-constexpr int FW_THREADS = 256;
+// Accumulator + bias -> SiLU -> BF16 activations in the K = 256 operand layout
+// of the next layer.  16 warps: warp w reads the rows of lane quadrant w % 4
+// (tcgen05.ld reaches only its own quadrant) and the column quarter w / 4 (64
+// columns, two loads of 32; the second is in flight while the first chunk's
+// arithmetic runs).
+__device__ __forceinline__ void epi_silu(uint32_t tmem, const float *bias, unsigned char *act)
+{
+    const int warp = threadIdx.x >> 5, q = warp & 3, part = warp >> 2;
+    const int r = 32 * q + (threadIdx.x & 31);
+    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
+    const int cb = part * (NH / 4);
+    unsigned char *row = act + (r & 7) * 16 + (r >> 3) * (NH / 8) * 128;
+    uint32_t u0[32], u1[32];
+    tmem_ld32_issue(tb + (uint32_t)cb, u0);
+    tmem_wait32(u0);
+    tmem_ld32_issue(tb + (uint32_t)(cb + 32), u1);
+    silu_store32(u0, bias, row, cb);
+    tmem_wait32(u1);
+    silu_store32(u1, bias, row, cb + 32);
+}
+
+constexpr int FW_THREADS = 512;
 
 __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ X0,
                                                        const __nv_bfloat16 *__restrict__ W1,
@@ -432,17 +466,19 @@ __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat1
     // the 128 x 16 input block of a tile is 256 chunks of 16 bytes, one per
     // thread: chunk (row tid / 2, column half tid % 2); the next tile's chunk is
     // loaded into registers while the current tile runs its three layers
-    static_assert(FW_THREADS == TC_M * (NIN_P / 8), "one 16-byte input chunk per thread");
-    const int xr = tid >> 1, xc = tid & 1;
+    constexpr int XCH = TC_M * (NIN_P / 8);   // 16-byte input chunks per tile
+    static_assert(FW_THREADS >= XCH && FW_THREADS % 128 == 0, "input chunks and lane quadrants");
+    const bool xin = tid < XCH;
+    const int xr = (tid & (XCH - 1)) >> 1, xc = tid & 1;
     const int xoff = ((xr >> 3) * 2 + xc) * 128 + (xr & 7) * 16;
     uint4 xcur = make_uint4(0u, 0u, 0u, 0u);
-    if (blockIdx.x < ntiles)
+    if (xin && blockIdx.x < ntiles)
         xcur = *reinterpret_cast<const uint4 *>(X0 + (size_t)(blockIdx.x * TC_M + xr) * NIN_P + 8 * xc);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int m0 = tile * TC_M;
-        *reinterpret_cast<uint4 *>(sAct + xoff) = xcur;
+        if (xin) *reinterpret_cast<uint4 *>(sAct + xoff) = xcur;
         uint4 xnext = make_uint4(0u, 0u, 0u, 0u);
-        if (tile + (int)gridDim.x < ntiles)
+        if (xin && tile + (int)gridDim.x < ntiles)
             xnext = *reinterpret_cast<const uint4 *>(X0 + (size_t)((tile + gridDim.x) * TC_M + xr) * NIN_P + 8 * xc);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -466,12 +502,12 @@ __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat1
                 epi_silu(tmem, sb + layer * NH, sAct);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             } else {
-                // 48 output columns: chunks 0, 1 by the first column half, chunk 2 by the second
-                const int q = warp & 3, half = warp >> 2;
+                // 48 output columns: 16 for each of the column parts 0, 1, 2
+                const int q = warp & 3, part = warp >> 2;
                 const int row = m0 + 32 * q + lane;
                 const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
-#pragma unroll 1
-                for (int c0 = half ? 32 : 0; c0 < (half ? NOUT_P : 32); c0 += 16) {
+                if (part < NOUT_P / 16) {
+                    const int c0 = 16 * part;
                     uint32_t u[16];
                     tmem_ld16_issue(tb + (uint32_t)c0, u);
                     tmem_wait(u);
