@@ -352,6 +352,52 @@ int sur_set_backend(sur_ctx *s, int use_tcgen05);
  * copies), between CUDA events; ms_per_pass: per pass of all members. */
 int sur_bench_forward(sur_ctx *s, int n, int reps, double *ms_per_pass);
 
+/* The 40 statistics a surrogate row holds, from the snapshots of one run:
+ * E [n_snap][n_shells] (E(k), k = 1..n_shells, Sec. 5.4; n_shells >= 64),
+ * g [n_snap][nbins] (velocity correlation, bin b centred at (b + 1/2) dr,
+ * Sec. 5.3; NaN for an empty bin), T [n_snap], vcom [n_snap] (mean |v_COM|
+ * of the agents).  With E and g averaged over the snapshots (g ignoring NaN;
+ * a bin NaN in every snapshot counts as 0):
+ *   out[0..31]  ln of E averaged over the shell pairs (2b+1, 2b+2)
+ *   out[32]     first r with g(r) <= 1/e (linear interpolation from g(0) = 1
+ *               over the bin centres), or the last centre when none
+ *   out[33]     trapezoid of g over r = 0 and the bin centres
+ *   out[34]     mean T
+ *   out[35]     least-squares slope of ln(E/E_1) on ln k, k = 1..10
+ *   out[36]     the same over k = 30..60
+ *   out[37]     k of the largest E(k)
+ *   out[38]     ln E_1
+ *   out[39]     mean of vcom
+ * (ln of a value below 1e-300 takes 1e-300.)  Host pointers; no device work. */
+int sur_targets(int n_snap, int n_shells, int nbins, double dr, const double *E, const double *g, const double *T,
+                const double *vcom, double out[40]);
+
+/* Simulation protocol behind a surrogate row (phi, gamma, zeta, f_p): a
+ * periodic box of side L with N_d = max(1, round(2 phi L^2)) agents
+ * (A = 25, kBT = 1, r_c = 1, kappa = 100, r0 = 0.5, dt = 0.01, m = 1), the
+ * paper's initial condition, `burn` steps, then `n_snap` snapshots `every`
+ * steps apart, each giving E(k) on an M x M grid (M >= 128), g(r) in bins of
+ * dr up to L/2, T and the mean |v_COM|. */
+typedef struct sur_protocol {
+    double L;          /* box side (48 in the training runs)               */
+    double dr;         /* correlation bin width (0.25)                      */
+    int32_t burn;      /* steps before the first snapshot (2000)           */
+    int32_t n_snap;    /* snapshots (10)                                    */
+    int32_t every;     /* steps between snapshots (200)                     */
+    int32_t M;         /* velocity-field grid side, even, >= 128 (128)      */
+    uint64_t seed;     /* row i runs with seed + i and replica i            */
+} sur_protocol;
+
+/* Prediction with simulation fallback (the deep ensemble's use): Y [n][40]
+ * is the ensemble mean, spread [n][40] the member standard deviation (may be
+ * NULL); a row whose largest relative spread max_t spread / (|mean| + 1)
+ * exceeds `threshold` is answered instead by running the protocol on the
+ * simulator (dpd_* on the surrogate's stream) and reducing it with
+ * sur_targets, and used_fallback[i] = 1 (else 0).  n <= max_rows.  Host
+ * pointers.  Synchronises. */
+int sur_query(sur_ctx *s, const float *X, int n, float threshold, const sur_protocol *proto, float *Y,
+              float *spread, int32_t *used_fallback);
+
 #ifdef __cplusplus
 }
 #endif

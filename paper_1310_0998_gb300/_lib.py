@@ -65,6 +65,18 @@ class DpdInfo(ctypes.Structure):
     ]
 
 
+class SurProtocol(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_double),
+        ("dr", ctypes.c_double),
+        ("burn", ctypes.c_int32),
+        ("n_snap", ctypes.c_int32),
+        ("every", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -119,6 +131,8 @@ def _declare(L):
         "sur_predict": ([vp, vp, c_int, vp, vp], c_int),
         "sur_set_backend": ([vp, c_int], c_int),
         "sur_bench_forward": ([vp, c_int, c_int, P(d)], c_int),
+        "sur_targets": ([c_int, c_int, c_int, d, vp, vp, vp, vp, vp], c_int),
+        "sur_query": ([vp, vp, c_int, ctypes.c_float, P(SurProtocol), vp, vp, vp], c_int),
     }
     for name, (args, res) in sig.items():
         if hasattr(L, name):

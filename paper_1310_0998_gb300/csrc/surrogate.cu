@@ -961,4 +961,149 @@ int sur_predict(sur_ctx *s, const float *X, int n, float *Y, float *spread)
     return DPD_OK;
 }
 
+
+static double ls_slope(const double *lnk, const double *y, int n)
+{
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int i = 0; i < n; ++i) {
+        sx += lnk[i];
+        sy += y[i];
+        sxx += lnk[i] * lnk[i];
+        sxy += lnk[i] * y[i];
+    }
+    return (n * sxy - sx * sy) / (n * sxx - sx * sx);
+}
+
+int sur_targets(int n_snap, int n_shells, int nbins, double dr, const double *E, const double *g, const double *T,
+                const double *vcom, double out[40])
+{
+    if (n_snap < 1 || n_shells < 64 || nbins < 1 || !(dr > 0) || !E || !g || !T || !vcom || !out)
+        return DPD_ERR_INVALID_ARG;
+    std::vector<double> Em(n_shells, 0.0), gm(nbins, 0.0);
+    for (int k = 0; k < n_shells; ++k) {
+        for (int s = 0; s < n_snap; ++s) Em[k] += E[(size_t)s * n_shells + k];
+        Em[k] /= n_snap;
+    }
+    for (int b = 0; b < nbins; ++b) {
+        double sum = 0;
+        int c = 0;
+        for (int s = 0; s < n_snap; ++s) {
+            const double v = g[(size_t)s * nbins + b];
+            if (!std::isnan(v)) { sum += v; ++c; }
+        }
+        gm[b] = c ? sum / c : 0.0;
+    }
+    for (int b = 0; b < 32; ++b) out[b] = std::log(std::max(0.5 * (Em[2 * b] + Em[2 * b + 1]), 1e-300));
+    // g over r = 0 (g = 1) and the bin centres
+    const double ie = std::exp(-1.0);
+    double xi = (nbins - 0.5) * dr, area = 0.0;
+    bool found = false;
+    double r_prev = 0.0, g_prev = 1.0;
+    for (int b = 0; b < nbins; ++b) {
+        const double r = (b + 0.5) * dr, gv = gm[b];
+        area += 0.5 * (gv + g_prev) * (r - r_prev);
+        if (!found && gv <= ie) {
+            const double f = (g_prev - ie) / std::max(g_prev - gv, 1e-300);
+            xi = r_prev + f * (r - r_prev);
+            found = true;
+        }
+        r_prev = r;
+        g_prev = gv;
+    }
+    out[32] = xi;
+    out[33] = area;
+    double t = 0, vc = 0;
+    for (int s = 0; s < n_snap; ++s) { t += T[s]; vc += vcom[s]; }
+    out[34] = t / n_snap;
+    double lnk[64], y[64];
+    for (int i = 0; i < 10; ++i) { lnk[i] = std::log((double)(i + 1)); y[i] = std::log(Em[i] / Em[0]); }
+    out[35] = ls_slope(lnk, y, 10);
+    for (int i = 0; i < 31; ++i) { lnk[i] = std::log((double)(30 + i)); y[i] = std::log(Em[29 + i] / Em[0]); }
+    out[36] = ls_slope(lnk, y, 31);
+    int kmax = 0;
+    for (int k = 1; k < n_shells; ++k)
+        if (Em[k] > Em[kmax]) kmax = k;
+    out[37] = kmax + 1;
+    out[38] = std::log(std::max(Em[0], 1e-300));
+    out[39] = vc / n_snap;
+    return DPD_OK;
+}
+
+// One fallback run of the protocol for the row (phi, gamma, zeta, f_p).
+static int sur_simulate_row(void *stream, const float *x, const sur_protocol *pr, uint64_t seed, uint32_t replica,
+                            double out[40])
+{
+    dpd_params p;
+    std::memset(&p, 0, sizeof p);
+    const long long nd = std::max(1LL, std::llround(2.0 * (double)x[0] * pr->L * pr->L));
+    p.L = pr->L;
+    p.n_beads = 2 * nd;
+    p.a = 25.0;
+    p.gamma = x[1];
+    p.kBT = 1.0;
+    p.rc = 1.0;
+    p.k_bond = 100.0;
+    p.r0 = 0.5;
+    p.f_p = x[3];
+    p.zeta = x[2];
+    p.dt = 0.01;
+    p.mass = 1.0;
+    p.seed = seed;
+    p.replica = replica;
+    p.exclude_bonded = 1;
+    dpd_ctx *c = nullptr;
+    int rc = dpd_create(&p, stream, &c);
+    if (rc) return rc;
+    const int nsh = pr->M / 2, nbins = (int)(pr->L / 2 / pr->dr);
+    std::vector<double> E((size_t)pr->n_snap * nsh), g((size_t)pr->n_snap * std::max(nbins, 1)), T(pr->n_snap),
+        vc(pr->n_snap);
+    std::vector<float> v((size_t)2 * p.n_beads);
+    int64_t st = 0;
+    rc = dpd_init_random(c, seed);
+    if (!rc) rc = dpd_step(c, pr->burn);
+    for (int s = 0; s < pr->n_snap && !rc; ++s) {
+        rc = dpd_step(c, pr->every);
+        if (!rc) rc = dpd_energy_spectrum(c, pr->M, 0.0, &E[(size_t)s * nsh]);
+        if (!rc) rc = dpd_velocity_correlation(c, pr->dr, nbins, &g[(size_t)s * nbins], nullptr, nullptr, nullptr);
+        if (!rc) rc = dpd_temperature(c, &T[s]);
+        if (!rc) rc = dpd_get_state(c, nullptr, v.data(), nullptr, &st, DPD_HOST);
+        if (!rc) {
+            double m = 0;
+            for (long long a = 0; a < nd; ++a) {
+                const double ux = 0.5 * ((double)v[4 * a] + v[4 * a + 2]), uy = 0.5 * ((double)v[4 * a + 1] + v[4 * a + 3]);
+                m += std::sqrt(ux * ux + uy * uy);
+            }
+            vc[s] = m / nd;
+        }
+    }
+    dpd_destroy(c);
+    if (!rc) rc = sur_targets(pr->n_snap, nsh, nbins, pr->dr, E.data(), g.data(), T.data(), vc.data(), out);
+    return rc;
+}
+
+int sur_query(sur_ctx *s, const float *X, int n, float threshold, const sur_protocol *proto, float *Y,
+              float *spread, int32_t *used_fallback)
+{
+    if (!s || !X || !Y || !used_fallback || !proto || n < 1 || n > s->cap) return DPD_ERR_INVALID_ARG;
+    if (!(proto->L >= 3.0) || !(proto->dr > 0) || proto->burn < 0 || proto->n_snap < 1 || proto->every < 0 ||
+        proto->M < 128 || (proto->M & 1) || (int)(proto->L / 2 / proto->dr) < 1)
+        return DPD_ERR_INVALID_ARG;
+    std::vector<float> S((size_t)n * NOUT);
+    int rc = sur_predict(s, X, n, Y, S.data());
+    if (rc) return rc;
+    for (int i = 0; i < n && !rc; ++i) {
+        float rel = 0.f;
+        for (int t = 0; t < NOUT; ++t)
+            rel = std::max(rel, S[(size_t)i * NOUT + t] / (std::fabs(Y[(size_t)i * NOUT + t]) + 1.0f));
+        used_fallback[i] = rel > threshold ? 1 : 0;
+        if (used_fallback[i]) {
+            double out[NOUT];
+            rc = sur_simulate_row(s->st, X + 4 * (size_t)i, proto, proto->seed + (uint64_t)i, (uint32_t)i, out);
+            for (int t = 0; t < NOUT && !rc; ++t) Y[(size_t)i * NOUT + t] = (float)out[t];
+        }
+    }
+    if (spread) std::memcpy(spread, S.data(), sizeof(float) * (size_t)n * NOUT);
+    return rc;
+}
+
 }  // extern "C"

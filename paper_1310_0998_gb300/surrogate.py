@@ -25,8 +25,6 @@ member spread exceeds a threshold is answered by running the simulation.
 from __future__ import annotations
 
 import ctypes
-import math
-import warnings
 
 import numpy as np
 
@@ -38,40 +36,16 @@ SUR_L = 48.0
 BASE = dict(a=25.0, kBT=1.0, rc=1.0, k_bond=100.0, r0=0.5, dt=0.01)
 
 
-def _slope(k, E):
-    y = np.log(E / E[0])
-    A = np.stack([np.log(k), np.ones_like(k)], axis=1)
-    return float(np.linalg.lstsq(A, y, rcond=None)[0][0])
-
-
 def targets(E_snaps, g_snaps, T_snaps, vcom_snaps, dr):
-    """The 40 statistics from per-snapshot E(k) [s, 64], g(r) [s, nb], T [s],
-    mean |v_COM| [s]."""
-    E = np.mean(np.asarray(E_snaps), axis=0)
-    with warnings.catch_warnings():
-        warnings.simplefilter("ignore", RuntimeWarning)   # bins with no pairs in any snapshot stay NaN
-        g = np.nanmean(np.asarray(g_snaps), axis=0)
+    """The 40 statistics from per-snapshot E(k) [s, >= 64], g(r) [s, nb], T
+    [s], mean |v_COM| [s] (sur_targets of the library)."""
+    E = np.ascontiguousarray(E_snaps, np.float64)
+    g = np.ascontiguousarray(g_snaps, np.float64)
+    T = np.ascontiguousarray(T_snaps, np.float64).ravel()
+    vc = np.ascontiguousarray(vcom_snaps, np.float64).ravel()
     out = np.zeros(NOUT, np.float64)
-    Epair = 0.5 * (E[0::2] + E[1::2])
-    out[0:32] = np.log(np.maximum(Epair[:32], 1e-300))
-    r = (np.arange(g.size) + 0.5) * dr
-    rr = np.concatenate([[0.0], r])
-    gg = np.concatenate([[1.0], np.nan_to_num(g, nan=0.0)])
-    below = np.nonzero(gg <= 1.0 / math.e)[0]
-    if below.size:
-        i = below[0]
-        f = (gg[i - 1] - 1.0 / math.e) / max(gg[i - 1] - gg[i], 1e-300)
-        out[32] = rr[i - 1] + f * (rr[i] - rr[i - 1])
-    else:
-        out[32] = rr[-1]
-    out[33] = float(np.sum(0.5 * (gg[1:] + gg[:-1]) * np.diff(rr)))
-    out[34] = float(np.mean(T_snaps))
-    k = np.arange(1, E.size + 1, dtype=np.float64)
-    out[35] = _slope(k[:10], E[:10])
-    out[36] = _slope(k[29:60], E[29:60])
-    out[37] = float(np.argmax(E) + 1)
-    out[38] = float(np.log(max(E[0], 1e-300)))
-    out[39] = float(np.mean(vcom_snaps))
+    check(_lib.lib().sur_targets(E.shape[0], E.shape[1], g.shape[1], float(dr), _lib.ptr(E), _lib.ptr(g),
+                                 _lib.ptr(T), _lib.ptr(vc), _lib.ptr(out)), "sur_targets")
     return out
 
 
@@ -184,15 +158,19 @@ class Surrogate:
 
     def query(self, X, threshold, simulate_kw=None):
         """Predictions; rows whose largest relative member spread (spread /
-        (|mean| + 1)) exceeds `threshold` are answered by simulation.
-        Returns (Y, used_fallback [n] bool)."""
-        Y, S = self.predict(X)
-        rel = np.max(S / (np.abs(Y) + 1.0), axis=1)
-        fb = rel > threshold
-        if np.any(fb):
-            Y = Y.astype(np.float64)
-            Y[fb] = simulate(np.asarray(X)[fb], batched=False, **(simulate_kw or {}))
-        return Y, fb
+        (|mean| + 1)) exceeds `threshold` are answered by the library running
+        the simulation protocol (sur_query; simulate_kw: L, burn, n_snap,
+        every, M, dr, seed as in simulate).  Returns (Y, used_fallback [n] bool)."""
+        kw = dict(L=SUR_L, burn=2000, n_snap=10, every=200, M=128, dr=0.25, seed=0)
+        kw.update(simulate_kw or {})
+        pr = _lib.SurProtocol(float(kw["L"]), float(kw["dr"]), int(kw["burn"]), int(kw["n_snap"]),
+                              int(kw["every"]), int(kw["M"]), int(kw["seed"]))
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.zeros((X.shape[0], NOUT), np.float32)
+        fb = np.zeros(X.shape[0], np.int32)
+        check(self._lib.sur_query(self._h, _lib.ptr(X), X.shape[0], ctypes.c_float(threshold), ctypes.byref(pr),
+                                  _lib.ptr(Y), None, _lib.ptr(fb)), "sur_query")
+        return Y, fb.astype(bool)
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -16,7 +16,7 @@ def _declared():
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
-        for m in re.finditer(r"\b((?:dpd|ens|sur)_[A-Za-z0-9_]+)\s*\(", src):
+        for m in re.finditer(r"\b((?:dpd3?|ens|sur)_[A-Za-z0-9_]+)\s*\(", src):
             names.add(m.group(1))
     return sorted(names)
 

@@ -198,11 +198,13 @@ def test_query_falls_back_to_simulation():
         # outside the training inputs in ln gamma and ln zeta
         far = np.array([[0.3, 0.05, 20.0, 0.5]], np.float32)
         kw = dict(L=16.0, burn=20, n_snap=2, every=10)
-        Yq, fb = s.query(np.concatenate([X[:1], far]), threshold=threshold, simulate_kw=kw)
+        rows = np.concatenate([X[:1], far])
+        Yq, fb = s.query(rows, threshold=threshold, simulate_kw=kw)
         assert not fb[0] and fb[1]
         np.testing.assert_allclose(Yq[0], P[0], rtol=1e-6)
-        ref = simulate(far, batched=False, **kw)
-        _close_stats(Yq[1], ref[0])
+        # the fallback runs row i with seed + i and replica i, as simulate does
+        ref = simulate(rows, batched=False, **kw)
+        _close_stats(Yq[1], ref[1])
     finally:
         s.close()
 
