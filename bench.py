@@ -146,7 +146,7 @@ def cpu_oracle_rate(L, n_beads, budget_s=12.0, seed=0):
     return rate, oracle.num_threads(), f"{steps} steps of the FP64 cell-list oracle on a {n_beads}-bead box (L={L:g}, density 3), {t2 - t0:.1f} s"
 
 
-def ensemble_leg(R, steps, warmup, seed=0, variant=0):
+def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0):
     """C4: R replicas drawn from the uneven distribution (box side U(32, 192),
     area fraction U(0.05, 0.6), gamma log-U(0.5, 50), zeta log-U(0.005, 2),
     f_p U(0.5, 2)).  Times `steps` steps of the batched persistent kernel and
@@ -157,7 +157,7 @@ def ensemble_leg(R, steps, warmup, seed=0, variant=0):
     for r, e in enumerate(synth.ensemble_points(R, seed)):
         pts.append(dict(a=PHYS["a"], kBT=PHYS["kBT"], rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"],
                         dt=PHYS["dt"], L=e["L"], n_beads=2 * e["n_dimers"], gamma=e["gamma"], zeta=e["zeta"],
-                        f_p=e["fp"], seed=seed + r, replica=r, variant=variant))
+                        f_p=e["fp"], seed=seed + r, replica=r, variant=variant, tile=tile))
     beads = sum(p["n_beads"] for p in pts)
     ens = Ensemble(pts)
     ens.init_random(seed)
@@ -212,7 +212,7 @@ def three_d_leg(steps=20, warmup=3, L=64.0, seed=0):
     return {"beads": nb, "L": L, "steps": steps, "particle_steps_per_s": rate, "ms_per_step": 1e3 * dt / steps,
             "roofline": {"bound": "alu", "achieved": OPS_PER_BEAD_STEP_3D * rate / 1e12, "peak": alu_peak / 1e12,
                          "unit": "Tops/s", "frac": OPS_PER_BEAD_STEP_3D * rate / alu_peak},
-            "timing": "wall clock around synchronised steps (scan, scatter, force per step)"}
+            "timing": "wall clock around synchronised steps (scan, scatter, pair forces, integration per step)"}
 
 
 def surrogate_leg(n_train=64, n_test=16, seed=0):
@@ -454,7 +454,8 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and not args.no_ensemble:
-        line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup, variant=args.variant)
+        line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup, variant=args.variant,
+                                        tile=args.tile)
     if rank == 0 and not args.no_surrogate:
         line["surrogate"] = surrogate_leg()
     if rank == 0 and not args.no_3d:

@@ -16,13 +16,17 @@
 //   counts, cstart  cell populations and their exclusive scan (the same
 //                   decoupled look-back scan as the 2D path)
 //   C_p, C_v, C_f   canonical (X_s, v_s, f_s) in id order after each call
-// One step: scan, scatter, then one thread per bead walks the full 3x3x3
-// stencil (every pair is evaluated from both sides with the same random
-// number, so each pair force is antisymmetric bit for bit; the pairs inside
-// r_c go through a warp queue so that their arithmetic runs on full warps),
-// adds bond,
-// propulsion and drag, does the second half-kick, the FP64 thermo partials,
-// the next half-kick and drift, and bins the new position.
+//   F    float4[N]  pair-force sums of the current step by sorted slot (kept
+//                   zero between steps)
+// One step: scan, scatter, pair forces, integration.  The pair kernel gives
+// one thread per bead the half stencil (the rest of its cell and the 13
+// cells ahead of it), so every pair inside r_c is evaluated once; the pairs
+// go through a warp queue so that their arithmetic runs on full warps, the
+// force lands on the owner through shared memory and its reaction on the
+// partner through one float4 atomic into F (sorted order).  The integration
+// kernel reads and clears F, adds bond, propulsion and drag, does the second
+// half-kick, the FP64 thermo partials, the next half-kick and drift, and bins
+// the new position.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -37,6 +41,7 @@ struct Sys3 {
     Sys b;                      // geometry scalars, physics, keys, scan/thermo/error words
     uint4 *S_p, *U_p, *C_p;
     float4 *S_v, *U_v, *C_v, *C_f;
+    float4 *F;                  // pair-force sums per sorted slot (zero between steps)
     uint32_t *U_rank, *slot;
 };
 
@@ -124,11 +129,16 @@ __device__ __forceinline__ float pair_scalar3(const Sys &d, float r2, float rinv
 }
 
 // One queued pair (sorted slot q, owner lane o of this warp): the pair force
-// on the owner, accumulated in shared memory.
+// on the owner, accumulated in shared memory, and its reaction on q, added to
+// q's sum in global memory (Newton-3: every pair is evaluated once).
 __device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const uint4 *pis, const float4 *vis,
                                       float (*fs)[4], uint32_t s_lo, uint32_t s_hi)
 {
     const Sys &d = s.b;
+    if (q >= (uint32_t)d.n) {   // cannot happen: every queued slot was read below n
+        set_err_at(d, ERR_INTERNAL, 13, q, o, 0);
+        return;
+    }
     const uint4 pi = pis[o], pj = s.S_p[q];
     const float4 vi = vis[o], vj = s.S_v[q];
     const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
@@ -140,15 +150,16 @@ __device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const ui
     atomicAdd(&fs[o][0], F * ex);
     atomicAdd(&fs[o][1], F * ey);
     atomicAdd(&fs[o][2], F * ez);
+    atomicAdd(&s.F[q], make_float4(-F * ex, -F * ey, -F * ez, 0.f));
 }
 
-// Thread per bead over the full 3x3x3 stencil.  The lanes of a warp test their
-// candidates in step (one per lane per iteration, as many iterations as the
-// longest cell range in the warp) and push the pairs inside r_c, as (slot,
-// owner lane), into the warp's queue; every 32 queued pairs the whole warp
-// evaluates Philox and the force together, so that arithmetic runs with every
-// lane busy whatever the neighbour counts.
-__global__ void __launch_bounds__(256, 5) k3_force(Sys3 s, int flags)
+// Pair forces, one thread per bead over the half stencil: the rest of its own
+// cell and the 13 cells ahead of it in (z, y, x) order, so that every pair
+// inside r_c is met once (n_c >= 3).  The lanes of a warp test their
+// candidates in step and push the pairs inside r_c, as (slot, owner lane),
+// into the warp's queue; every 32 queued pairs the whole warp evaluates
+// Philox and the force together.  Sums go to F (sorted order).
+__global__ void __launch_bounds__(256, 5) k3_pairs(Sys3 s)
 {
     const Sys &d = s.b;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,7 +170,6 @@ __global__ void __launch_bounds__(256, 5) k3_force(Sys3 s, int flags)
     __shared__ uint4 s_pi[8][32];
     __shared__ float4 s_vi[8][32];
     __shared__ float s_f[8][32][4];
-    float ke = 0.f, px = 0.f, py = 0.f, pz = 0.f;
     const bool active = g < d.n;
     const long long step = *d.step;
     const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
@@ -176,66 +186,83 @@ __global__ void __launch_bounds__(256, 5) k3_force(Sys3 s, int flags)
     __syncwarp();
     const int cx = cell_coord(d, pi.x), cy = cell_coord(d, pi.y), cz = cell_coord(d, pi.z);
     int qn = 0;
-    for (int oz = -1; oz <= 1; ++oz) {
-        int z = cz + oz;
+    // entry 0: own cell after g; entries 1..13: (dz, dy, dx) > 0 lexicographically
+#pragma unroll 1
+    for (int e = 0; e < 14; ++e) {
+        int oz = 0, oy = 0, ox = 0;
+        if (e >= 5) { oz = 1; oy = (e - 5) / 3 - 1; ox = (e - 5) % 3 - 1; }
+        else if (e >= 2) { oy = 1; ox = e - 3; }
+        else if (e == 1) { ox = 1; }
+        int x = cx + ox, y = cy + oy, z = cz + oz;
+        x += x < 0 ? d.nc : (x >= d.nc ? -d.nc : 0);
+        y += y < 0 ? d.nc : (y >= d.nc ? -d.nc : 0);
         z += z < 0 ? d.nc : (z >= d.nc ? -d.nc : 0);
-        for (int oy = -1; oy <= 1; ++oy) {
-            int y = cy + oy;
-            y += y < 0 ? d.nc : (y >= d.nc ? -d.nc : 0);
-            const int row = (z * d.nc + y) * d.nc;
-            for (int ox = -1; ox <= 1; ++ox) {
-                int x = cx + ox;
-                x += x < 0 ? d.nc : (x >= d.nc ? -d.nc : 0);
-                uint32_t b = 0, e = 0;
-                if (active) {
-                    const int c = row + x;
-                    b = min(d.cstart[c], n);
-                    e = min(max(d.cstart[c + 1], b), n);
+        uint32_t b = 0, en = 0;
+        if (active) {
+            const int c = (z * d.nc + y) * d.nc + x;
+            b = min(d.cstart[c], n);
+            en = min(max(d.cstart[c + 1], b), n);
+            if (e == 0) b = min((uint32_t)g + 1u, en);
+        }
+        const int len = (int)(en - b);
+        const int maxlen = __reduce_max_sync(FULL, (unsigned)len);
+        for (int t = 0; t < maxlen; ++t) {
+            const uint32_t q = b + (uint32_t)t;
+            bool hit = false;
+            if (t < len) {
+                const uint4 pj = s.S_p[q];
+                if (pj.w != pid) {
+                    const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    hit = (r2 < d.rc2) & (r2 > 0.f);
                 }
-                const int len = (int)(e - b);
-                const int maxlen = __reduce_max_sync(FULL, len);
-                for (int t = 0; t < maxlen; ++t) {
-                    const uint32_t q = b + (uint32_t)t;
-                    bool hit = false;
-                    if (t < len && q != (uint32_t)g) {
-                        const uint4 pj = s.S_p[q];
-                        if (pj.w != pid) {
-                            const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y),
-                                        dz = mdiff(d, pi.z, pj.z);
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            hit = (r2 < d.rc2) & (r2 > 0.f);
-                        }
-                    }
-                    const unsigned m = __ballot_sync(FULL, hit);
-                    if (hit) {
-                        const int pos = qn + __popc(m & lt);
-                        s_q[warp][pos] = q;
-                        s_ql[warp][pos] = (unsigned char)lane;
-                    }
-                    qn += __popc(m);
-                    __syncwarp();
-                    if (qn >= 32) {
-                        const uint32_t mq = s_q[warp][lane];
-                        const int mo = s_ql[warp][lane];
-                        const uint32_t cq = s_q[warp][32 + lane];
-                        const unsigned char co = s_ql[warp][32 + lane];
-                        __syncwarp();
-                        if (lane < qn - 32) {
-                            s_q[warp][lane] = cq;
-                            s_ql[warp][lane] = co;
-                        }
-                        qn -= 32;
-                        eval3(s, mq, mo, s_pi[warp], s_vi[warp], s_f[warp], s_lo, s_hi);
-                        __syncwarp();
-                    }
+            }
+            const unsigned m = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int pos = qn + __popc(m & lt);
+                s_q[warp][pos] = q;
+                s_ql[warp][pos] = (unsigned char)lane;
+            }
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                const uint32_t mq = s_q[warp][lane];
+                const int mo = s_ql[warp][lane];
+                const uint32_t cq = s_q[warp][32 + lane];
+                const unsigned char co = s_ql[warp][32 + lane];
+                __syncwarp();
+                if (lane < qn - 32) {
+                    s_q[warp][lane] = cq;
+                    s_ql[warp][lane] = co;
                 }
+                qn -= 32;
+                eval3(s, mq, mo, s_pi[warp], s_vi[warp], s_f[warp], s_lo, s_hi);
+                __syncwarp();
             }
         }
     }
     if (lane < qn) eval3(s, s_q[warp][lane], s_ql[warp][lane], s_pi[warp], s_vi[warp], s_f[warp], s_lo, s_hi);
     __syncwarp();
-    if (active) {
-        float fx = s_f[warp][lane][0], fy = s_f[warp][lane][1], fz = s_f[warp][lane][2];
+    if (active) atomicAdd(&s.F[g], make_float4(s_f[warp][lane][0], s_f[warp][lane][1], s_f[warp][lane][2], 0.f));
+}
+
+// Everything after the pair sums, one thread per sorted slot: the pair force
+// (reset to zero for the next step), bond and propulsion (partner id ^ 1),
+// drag on the half-step velocity, the second half-kick, FP64 thermo
+// partials, the next half-kick and drift, and the binning of the new position.
+__global__ void __launch_bounds__(256) k3_integrate(Sys3 s, int flags)
+{
+    const Sys &d = s.b;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    float ke = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+    const uint32_t n = (uint32_t)d.n;
+    if (g < d.n) {
+        const uint4 pi = s.S_p[g];
+        const float4 vi = s.S_v[g];
+        const uint32_t id = pi.w;
+        const float4 fp = s.F[g];
+        s.F[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float fx = fp.x, fy = fp.y, fz = fp.z;
         // bond and propulsion (partner id ^ 1), drag on the half-step velocity
         const uint32_t ps = s.slot[id ^ 1u];
         if (ps < n) {
@@ -346,7 +373,8 @@ static void iteration3(dpd3_ctx *c, int flags)
     const int g = (c->s.b.n + 255) / 256;
     k3_scan<<<c->nscan, SCAN_NT, 0, c->st>>>(c->s.b, c->nscan);
     k3_scatter<<<g, 256, 0, c->st>>>(c->s);
-    k3_force<<<g, 256, 0, c->st>>>(c->s, flags);
+    k3_pairs<<<g, 256, 0, c->st>>>(c->s);
+    k3_integrate<<<g, 256, 0, c->st>>>(c->s, flags);
 }
 
 extern "C" {
@@ -381,7 +409,8 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
                  o_Cp = take(16 * n), o_Cv = take(16 * n), o_Cf = take(16 * n), o_rank = take(4 * n),
                  o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
                  o_th = take(32 * (size_t)THERMO_CAP), o_step = take(8), o_err = take(4), o_einfo = take(32),
-                 o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(48 * n);
+                 o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(48 * n),
+                 o_F = take(16 * n);
     if (cudaMalloc(&c->pool, off) != cudaSuccess || cudaMallocHost((void **)&c->h_pin, 4096) != cudaSuccess) {
         dpd3_destroy(c);
         return DPD_ERR_OOM;
@@ -391,6 +420,7 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
     c->s.U_p = (uint4 *)(b + o_Up); c->s.U_v = (float4 *)(b + o_Uv);
     c->s.C_p = (uint4 *)(b + o_Cp); c->s.C_v = (float4 *)(b + o_Cv); c->s.C_f = (float4 *)(b + o_Cf);
     c->s.U_rank = (uint32_t *)(b + o_rank); c->s.slot = (uint32_t *)(b + o_slot);
+    c->s.F = (float4 *)(b + o_F);   // zeroed with the pool; k3_integrate keeps it zero between steps
     d.slot = c->s.slot;
     d.counts = (uint32_t *)(b + o_cnt); d.cstart = (uint32_t *)(b + o_cst);
     d.thermo = (double *)(b + o_th); d.step = (long long *)(b + o_step);
