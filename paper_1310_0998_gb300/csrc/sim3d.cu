@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "dpd.h"
 #include "sim_host.h"
@@ -42,6 +43,9 @@ struct Sys3 {
     uint4 *S_p, *U_p, *C_p;
     float4 *S_v, *U_v, *C_v, *C_f;
     float4 *F;                  // pair-force sums per sorted slot (zero between steps)
+    float4 *S_off;              // offset from the own cell's corner (length units) + id bits, sorted
+    const uint32_t *corner;     // fixed-point corner ceil(c 2^32 / n_c) of cell coordinate c
+    float rc2f;                 // r_c^2 (1 + 1e-5): candidate filter, never narrower than the exact test
     uint32_t *U_rank, *slot;
 };
 
@@ -77,6 +81,10 @@ __global__ void k3_scatter(Sys3 s)
     s.S_p[dst] = p;
     s.S_v[dst] = s.U_v[k];
     s.slot[p.w] = dst;
+    const Sys &d = s.b;
+    s.S_off[dst] = make_float4((float)(int)(p.x - s.corner[cell_coord(d, p.x)]) * d.ulen,
+                               (float)(int)(p.y - s.corner[cell_coord(d, p.y)]) * d.ulen,
+                               (float)(int)(p.z - s.corner[cell_coord(d, p.z)]) * d.ulen, __uint_as_float(p.w));
 }
 
 // Double positions [N][3] and float velocities [N][3] (id order) -> U.
@@ -143,6 +151,7 @@ __device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const ui
     const float4 vi = vis[o], vj = s.S_v[q];
     const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
     const float r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 < d.rc2) || !(r2 > 0.f)) return;   // the walk's filter is a little wider than r_c
     const float rinv = rsqrtf(r2);
     const float ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;   // e = (x_i - x_j)/r
     const float dve = (vi.x - vj.x) * ex + (vi.y - vj.y) * ey + (vi.z - vj.z) * ez;
@@ -185,6 +194,9 @@ __global__ void __launch_bounds__(256, 5) k3_pairs(Sys3 s)
     s_f[warp][lane][2] = 0.f;
     __syncwarp();
     const int cx = cell_coord(d, pi.x), cy = cell_coord(d, pi.y), cz = cell_coord(d, pi.z);
+    // the walk tests separations from cell-corner offsets (no conversion per
+    // candidate); a pair it passes is tested again exactly before evaluation
+    const float4 oi = active ? s.S_off[g] : make_float4(0.f, 0.f, 0.f, 0.f);
     int qn = 0;
     // entry 0: own cell after g; entries 1..13: (dz, dy, dx) > 0 lexicographically
 #pragma unroll 1
@@ -206,16 +218,16 @@ __global__ void __launch_bounds__(256, 5) k3_pairs(Sys3 s)
         }
         const int len = (int)(en - b);
         const int maxlen = __reduce_max_sync(FULL, (unsigned)len);
+        // bead i seen from the corner of the cell (ox, oy, oz) cells away
+        const float pix = oi.x - (float)ox * d.cs, piy = oi.y - (float)oy * d.cs, piz = oi.z - (float)oz * d.cs;
         for (int t = 0; t < maxlen; ++t) {
             const uint32_t q = b + (uint32_t)t;
             bool hit = false;
             if (t < len) {
-                const uint4 pj = s.S_p[q];
-                if (pj.w != pid) {
-                    const float dx = mdiff(d, pi.x, pj.x), dy = mdiff(d, pi.y, pj.y), dz = mdiff(d, pi.z, pj.z);
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    hit = (r2 < d.rc2) & (r2 > 0.f);
-                }
+                const float4 oj = s.S_off[q];
+                const float dx = pix - oj.x, dy = piy - oj.y, dz = piz - oj.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                hit = (r2 < s.rc2f) & (__float_as_uint(oj.w) != pid) & (q != (uint32_t)g);
             }
             const unsigned m = __ballot_sync(FULL, hit);
             if (hit) {
@@ -410,7 +422,7 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
                  o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
                  o_th = take(32 * (size_t)THERMO_CAP), o_step = take(8), o_err = take(4), o_einfo = take(32),
                  o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(48 * n),
-                 o_F = take(16 * n);
+                 o_F = take(16 * n), o_off = take(16 * n), o_corner = take(4 * (size_t)nc);
     if (cudaMalloc(&c->pool, off) != cudaSuccess || cudaMallocHost((void **)&c->h_pin, 4096) != cudaSuccess) {
         dpd3_destroy(c);
         return DPD_ERR_OOM;
@@ -421,6 +433,9 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
     c->s.C_p = (uint4 *)(b + o_Cp); c->s.C_v = (float4 *)(b + o_Cv); c->s.C_f = (float4 *)(b + o_Cf);
     c->s.U_rank = (uint32_t *)(b + o_rank); c->s.slot = (uint32_t *)(b + o_slot);
     c->s.F = (float4 *)(b + o_F);   // zeroed with the pool; k3_integrate keeps it zero between steps
+    c->s.S_off = (float4 *)(b + o_off);
+    c->s.corner = (const uint32_t *)(b + o_corner);
+    c->s.rc2f = (float)(p->rc * p->rc * (1.0 + 1e-5));
     d.slot = c->s.slot;
     d.counts = (uint32_t *)(b + o_cnt); d.cstart = (uint32_t *)(b + o_cst);
     d.thermo = (double *)(b + o_th); d.step = (long long *)(b + o_step);
@@ -429,7 +444,12 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
     d.S_xv = nullptr; d.S_id = nullptr; d.U_xv = nullptr; d.U_id = nullptr; d.U_rank = c->s.U_rank;
     d.C_xv = nullptr; d.C_f = nullptr; d.pcnt = nullptr; d.ovf = nullptr;
     c->stage = b + o_stage;
-    if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess || cudaStreamSynchronize(c->st) != cudaSuccess) {
+    std::vector<uint32_t> corner((size_t)nc);
+    for (int q = 0; q < nc; ++q)
+        corner[q] = (uint32_t)((((unsigned long long)q << 32) + (unsigned long long)(nc - 1)) / (unsigned long long)nc);
+    if (cudaMemsetAsync(c->pool, 0, off, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(b + o_corner, corner.data(), 4 * (size_t)nc, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
         dpd3_destroy(c);
         return DPD_ERR_CUDA;
     }
