@@ -110,15 +110,16 @@ template <int B>
 __global__ void k_kick_bin(Sys d)
 {
     __shared__ double s_red[3 * 33];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     Thermo3 th{0.f, 0.f, 0.f};
-    if (k < d.n) {
+    // grid-stride over the beads with a capped grid: the per-block FP64 thermo
+    // flush targets one address, and one flush per 256 beads serialised there
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
         const uint4 xv = d.C_xv[k];
         const float2 f = d.C_f[k];
         float vx = vbits(xv.z), vy = vbits(xv.w);
-        th.ke = vx * vx + vy * vy;
-        th.px = vx;
-        th.py = vy;
+        th.ke += vx * vx + vy * vy;
+        th.px += vx;
+        th.py += vy;
         vx += d.hdtm * f.x;
         vy += d.hdtm * f.y;
         const float ddx = d.dt * vx, ddy = d.dt * vy;
@@ -379,7 +380,7 @@ void launch_bin(const Sys &d, int B, cudaStream_t st)
 
 void launch_kick_bin(const Sys &d, int B, cudaStream_t st)
 {
-    const int g = (d.n + 255) / 256;
+    const int g = std::min((d.n + 255) / 256, 1024);
     switch (B) {
         case 4: k_kick_bin<4><<<g, 256, 0, st>>>(d); break;
         case 8: k_kick_bin<8><<<g, 256, 0, st>>>(d); break;
