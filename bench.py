@@ -188,6 +188,35 @@ def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0):
             "timing": "wall clock around each leg, synchronised; sequential = each replica alone, one after another"}
 
 
+def observables_leg(sim, nb, reps=5):
+    """Observables on the device (Secs. 5.3-5.4): E(k) at M = 128 on the main
+    box's state (agent centres of mass, windowed velocity field, the library's
+    own FFT, shell sums), and the all-pairs velocity correlation g(r) on a
+    196,608-bead box of side 256 (98,304 agents)."""
+    from paper_1310_0998_gb300 import Sim, synth
+    sim.energy_spectrum(128)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        sim.energy_spectrum(128)
+    t_spec = (time.perf_counter() - t0) / reps
+    Lv, nbv = 256.0, 196608
+    x, _ = synth.dimers(nbv // 2, Lv, PHYS["r0"], seed=1)
+    vel = synth.velocities(nbv, 1.0, seed=2)
+    with Sim(Lv, nbv, a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"], rc=PHYS["rc"], k_bond=PHYS["kbond"],
+             r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"], dt=PHYS["dt"]) as s:
+        s.set_positions(x, vel)
+        s.velocity_correlation(0.25, 512)
+        t0 = time.perf_counter()
+        s.velocity_correlation(0.25, 512)
+        t_vcf = time.perf_counter() - t0
+    na = nbv // 2
+    return {"spectrum_M": 128, "spectrum_agents": nb // 2, "spectrum_ms": 1e3 * t_spec,
+            "spectrum_state_gbs": 16.0 * nb / t_spec / 1e9,
+            "vcf_agents": na, "vcf_bins": 512, "vcf_ms": 1e3 * t_vcf,
+            "vcf_agent_pairs_per_s": na * (na - 1) / 2 / t_vcf,
+            "timing": "wall clock per synchronising call (device work and the copy of the result to the host)"}
+
+
 OPS_PER_BEAD_STEP_3D = 1200.0   # 40.5 half-stencil tests x 10 + 6.3 pairs x 115 + 70 integration
 
 
@@ -326,6 +355,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg")
     ap.add_argument("--no-3d", action="store_true", help="skip the three-dimensional leg")
+    ap.add_argument("--no-obs", action="store_true", help="skip the observables leg")
     ap.add_argument("--wexp", type=float, default=0.0,
                     help="exponent s of w in the dissipative/random forces (0 = 2, the printed form)")
     ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue, 3 grid-order queue")
@@ -458,6 +488,8 @@ def main():
                                         tile=args.tile)
     if rank == 0 and not args.no_surrogate:
         line["surrogate"] = surrogate_leg()
+    if rank == 0 and not args.no_obs:
+        line["observables"] = observables_leg(sim, nb)
     if rank == 0 and not args.no_3d:
         line["three_d"] = three_d_leg()
     if rank == 0 and not args.no_cpu:
