@@ -208,18 +208,33 @@ __global__ void __launch_bounds__(VCF_TILE) k_vcf(const double2 *c, const double
     if (a < na) {
         const double2 ca = c[a], va = v[a];
         const int jn = min(VCF_TILE, na - jb);
+        const double hL = 0.5 * L;
+        const double rmax2 = (double)nbins * dr * (double)nbins * dr * (1.0 + 1e-9);
+        const float inv_drf = (float)(1.0 / dr), nbf = (float)nbins;
         for (int q = 0; q < jn; ++q) {
             const int j = jb + q;
             if (j <= a) continue;
-            double dx = minimg_d(__dsub_rn(ca.x, sc[q].x), L);
-            double dy = minimg_d(__dsub_rn(ca.y, sc[q].y), L);
-            const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-            const double bf = floor(__ddiv_rn(r, dr));
-            if (bf < (double)nbins) {
-                const int b = (int)bf;
-                atomicAdd(&snum[b], __dadd_rn(__dmul_rn(va.x, sv[q].x), __dmul_rn(va.y, sv[q].y)));
-                atomicAdd(&scnt[b], 1ull);
+            // minimum image: agent centres lie on the L / 2^33 grid, so d / L never
+            // rounds onto +-1/2 and the comparison equals d - L rint(d / L)
+            double dx = __dsub_rn(ca.x, sc[q].x), dy = __dsub_rn(ca.y, sc[q].y);
+            dx = dx > hL ? __dsub_rn(dx, L) : (dx < -hL ? __dadd_rn(dx, L) : dx);
+            dy = dy > hL ? __dsub_rn(dy, L) : (dy < -hL ? __dadd_rn(dy, L) : dy);
+            const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            if (!(r2 < rmax2)) continue;   // beyond the last bin (a margin above it)
+            // bin floor(sqrt(r2) / dr): FP32 where the value is at least 1e-3 from
+            // a bin edge (its error here is ~1e-4), else the FP64 expression
+            const float tf = sqrtf((float)r2) * inv_drf;
+            const float fl = floorf(tf);
+            int b;
+            if (tf - fl > 1e-3f && fl + 1.0f - tf > 1e-3f && tf < nbf - 1e-3f) {
+                b = (int)fl;
+            } else {
+                const double bf = floor(__ddiv_rn(sqrt(r2), dr));
+                if (!(bf < (double)nbins)) continue;
+                b = (int)bf;
             }
+            atomicAdd(&snum[b], __dadd_rn(__dmul_rn(va.x, sv[q].x), __dmul_rn(va.y, sv[q].y)));
+            atomicAdd(&scnt[b], 1ull);
         }
     }
     __syncthreads();
