@@ -1,8 +1,9 @@
 """FP64 CPU oracle for the self-propelled DPD dimer model (arXiv:1310.0998).
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package:
-only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` do.  It shares no code with the CUDA library.
+only the tests, ``__graft_entry__.smoke()`` (``build()`` compiles it) and the
+CPU-baseline leg and reference arm of ``bench.py`` do.  It shares no code with
+the CUDA library.
 
 The particle dynamics (Sec. 2, Sec. 5) live in ``dpd_oracle.c`` (compiled with
 ``build()``); the observables of Sec. 5.3-5.4 live in ``observables.py`` (numpy,
