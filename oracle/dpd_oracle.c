@@ -5,7 +5,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
  * statement of what the GPU path computes.  Only the test-suite, the smoke
- * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * check and the CPU-baseline leg and reference arm of the benchmark may load
+ * it.  It shares no
  * code, header, constant table or helper with the CUDA library; the two are
  * written independently from the paper and from the published definition of
  * the Philox4x32-10 generator (Salmon, Moraes, Dror & Shaw, "Parallel random
