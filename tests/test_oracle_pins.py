@@ -336,3 +336,107 @@ def test_cell_rule_stencil_is_sufficient(orc):
         ddx = np.abs(cx[ii] - cx[jj]); ddx = np.minimum(ddx, nc - ddx)
         ddy = np.abs(cy[ii] - cy[jj]); ddy = np.minimum(ddy, nc - ddy)
         assert ddx.max(initial=0) <= 1 and ddy.max(initial=0) <= 1
+
+
+# --------------------------------------------------------------------------
+# Neighbour counts (reference for the bit-exact count tests) and the thermo
+# reductions, pinned on hand-built configurations
+# --------------------------------------------------------------------------
+
+def test_pair_counts_hand_built(orc):
+    """Beads placed by hand in a box of side 10 (r_c = 1): pairs at r well
+    inside r_c, just inside, just outside, inside the tie band around r_c,
+    exactly at r = 0, across the periodic boundary, and a bonded pair with the
+    exclusion switched on and off.  Expected counts are written down from the
+    geometry (Sec. 2.1: the pair force acts for r < r_c only; Sec. 2.2: bonded
+    beads have no other interaction)."""
+    L = 10.0
+    x = np.array([
+        [1.0, 1.0],    # 0: bonded to 1 at r = 0.5
+        [1.5, 1.0],    # 1
+        [1.0, 1.9],    # 2: r(0,2) = 0.9, r(1,2) = sqrt(0.25 + 0.81) > 1
+        [5.0, 5.0],    # 3: r(3,4) = 1 - 1e-3 (inside, outside the tie band)
+        [5.0, 5.999],  # 4
+        [7.0, 7.0],    # 5: r(5,6) = 1 + 1e-3 (outside)
+        [8.001, 7.0],  # 6
+        [3.0, 8.0],    # 7: r(7,8) = 1 - 1e-7: inside the tie band -> ambiguous
+        [3.0, 8.9999999],  # 8
+        [0.2, 5.0],    # 9: across x = 0: r(9,10) = 0.2 + 0.3 = 0.5
+        [9.7, 5.0],    # 10
+        [6.0, 2.0],    # 11: coincident with 12: r = 0 counts as no pair
+        [6.0, 2.0],    # 12
+        [8.5, 9.8],    # 13: across the corner: r(13,14) = sqrt(0.3^2+0.4^2) = 0.5
+        [8.8, 0.2],    # 14
+        [5.0, 5.9995],  # 15: near 3 and 4: r(3,15) = 0.9995 inside, r(4,15) = 5e-4 inside
+    ])
+    p = P(orc, L=L)
+    cnt, amb, tot = orc.pair_counts(p, x, tie=1e-6)
+    # pairs inside r_c: (0,2), (3,4), (9,10), (13,14), (3,15), (4,15); (0,1) excluded (bonded)
+    exp_cnt = np.zeros(16, np.uint32)
+    for i, j in [(0, 2), (3, 4), (9, 10), (13, 14), (3, 15), (4, 15)]:
+        exp_cnt[i] += 1
+        exp_cnt[j] += 1
+    exp_amb = np.zeros(16, np.uint32)
+    exp_amb[7] = exp_amb[8] = 1
+    np.testing.assert_array_equal(cnt, exp_cnt)
+    np.testing.assert_array_equal(amb, exp_amb)
+    assert tot == 6
+    # exclusion off: the bonded pair (0, 1) at r = 0.5 counts as well
+    cnt2, amb2, tot2 = orc.pair_counts(P(orc, L=L, exclude_bonded=0), x, tie=1e-6)
+    exp2 = exp_cnt.copy()
+    exp2[0] += 1
+    exp2[1] += 1
+    np.testing.assert_array_equal(cnt2, exp2)
+    np.testing.assert_array_equal(amb2, exp_amb)
+    assert tot2 == 7
+    # a tie band of 3e-3 r_c^2 swallows the pairs at r = 1 - 1e-3, 1 + 1e-3
+    # and 1 - 5e-4 (|r^2 - 1| = 2e-3, 2e-3, 1e-3) besides the one at 1 - 1e-7
+    cnt3, amb3, tot3 = orc.pair_counts(p, x, tie=3e-3)
+    assert tot3 == 4
+    np.testing.assert_array_equal(amb3[[3, 4, 5, 6, 7, 8, 15]], [2, 1, 1, 1, 1, 1, 1])
+    assert cnt3[3] == 0 and cnt3[4] == 1 and cnt3[15] == 1   # only (4, 15) at 5e-4 remains
+
+
+def test_pair_counts_brute_force_in_numpy(orc):
+    """Random dimers: the oracle's counts equal an independent numpy count of
+    the minimum-image pairs with r < r_c, bonded pairs excluded, ties removed."""
+    L = 6.0
+    x, _ = synth.dimers(60, L, 0.5, seed=11)
+    x = x.astype(np.float64)
+    cnt, amb, tot = orc.pair_counts(P(orc, L=L), x, tie=4e-6)
+    d = x[:, None, :] - x[None, :, :]
+    d -= L * np.rint(d / L)
+    r2 = (d ** 2).sum(-1)
+    n = x.shape[0]
+    idx = np.arange(n)
+    bonded = (idx[:, None] ^ 1) == idx[None, :]
+    off = ~np.eye(n, dtype=bool) & ~bonded
+    tie = off & (np.abs(r2 - 1.0) < 4e-6)
+    inside = off & ~tie & (r2 < 1.0) & (r2 > 0.0)
+    np.testing.assert_array_equal(cnt, inside.sum(1).astype(np.uint32))
+    np.testing.assert_array_equal(amb, tie.sum(1).astype(np.uint32))
+    assert tot == int(np.triu(inside, 1).sum())
+
+
+def test_thermo_two_beads_by_hand(orc):
+    """KE = 1/2 m sum |v|^2, P = m sum v and T = sum m |v|^2 / (2N - 2) for
+    two beads with v = (3, 4) and (-1, 2), m = 2: KE = 2 (25 + 5) / 2 = 30,
+    P = 2 (2, 6) = (4, 12), T = 2 * 30 / 2 = 30."""
+    ke, p, T = orc.thermo(np.zeros((2, 2)), np.array([[3.0, 4.0], [-1.0, 2.0]]), mass=2.0)
+    assert ke == 30.0
+    np.testing.assert_array_equal(p, [4.0, 12.0])
+    assert T == 30.0
+    # four beads at rest but one: T divides by 2N - 2 = 6
+    ke, p, T = orc.thermo(np.zeros((4, 2)), np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 0.0], [1.0, 1.0]]))
+    assert ke == 1.0 and T == 2.0 / 6.0
+    np.testing.assert_array_equal(p, [1.0, 1.0])
+
+
+def test_pair_counts_exactly_at_cutoff(orc):
+    """With no tie band a pair at exactly r = r_c has w = 0 and is not a
+    neighbour (r < r_c strictly); one a binary ulp closer is."""
+    L = 8.0
+    x = np.array([[2.0, 2.0], [2.0, 4.5], [3.0, 2.0], [6.0, 6.0], [6.0, 7.0 - 2.0 ** -40], [1.0, 6.0]])
+    cnt, amb, tot = orc.pair_counts(P(orc, L=L, exclude_bonded=0), x, tie=0.0)
+    assert tot == 1 and amb.sum() == 0
+    np.testing.assert_array_equal(cnt, [0, 0, 0, 1, 1, 0])
