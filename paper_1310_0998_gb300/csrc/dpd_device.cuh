@@ -44,6 +44,7 @@ struct Sys {
     int nc, ntx, n, ncells;
     float rc2, inv_rc, a, gamma, sig_r, kbond, r0, fp, zeta, dt, hdtm;
     float hwexp;                   // s/2 of w_R = w^(s/2) when gen_w
+    float rc2u, inv_rcu;           // r_c^2 in fixed-point units^2, and ulen / r_c
     int gen_w;                     // 1: dissipative weight exponent s != 2
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];   // Philox round keys key + r * (Weyl increments)
@@ -111,9 +112,9 @@ __device__ __forceinline__ float pair_noise(const Sys &d, uint32_t ia, uint32_t 
     // 2 (w0 >> 8) + 1 - 2^24, formed exactly in FP32 (every term is an
     // integer below 2^25 in magnitude with at most 24 significant bits)
     if (d.noise == 0) return fmaf((float)(c0 >> 8), 2.0f, 1.0f - 16777216.0f);
-    const float u1 = ((float)(c0 >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    const float u2 = ((float)(c1 >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float u1 = __fmul_rn(__fadd_rn((float)(c0 >> 8), 0.5f), 5.9604644775390625e-08f);
+    const float u2 = __fmul_rn(__fadd_rn((float)(c1 >> 8), 0.5f), 5.9604644775390625e-08f);
+    return __fmul_rn(__fsqrt_rn(__fmul_rn(-2.0f, logf(u1))), cospif(__fmul_rn(2.0f, u2)));
 }
 
 // ---------------------------------------------------------- cell geometry ----
@@ -132,14 +133,14 @@ __device__ __forceinline__ int cell_of(const Sys &d, int cx, int cy)
 // difference, one rounding in the conversion).
 __device__ __forceinline__ float mdiff(const Sys &d, uint32_t a, uint32_t b)
 {
-    return (float)(int)(a - b) * d.ulen;
+    return __fmul_rn((float)(int)(a - b), d.ulen);
 }
 
 // Fixed-point step of a coordinate by a displacement dx (|dx| < L/2):
 // rounded to the nearest unit, wrapped by unsigned overflow.
 __device__ __forceinline__ uint32_t fx_add(const Sys &d, uint32_t X, float dx)
 {
-    return X + (uint32_t)__float2int_rn(dx * d.inv_ulen);
+    return X + (uint32_t)__float2int_rn(__fmul_rn(dx, d.inv_ulen));
 }
 
 __device__ __forceinline__ float vbits(uint32_t u) { return __uint_as_float(u); }

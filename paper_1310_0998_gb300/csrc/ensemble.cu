@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
         for (int it = blockIdx.x; it < n_tiles; it += nb) {
             const uint32_t w = tiles[it];
             const Sys &d = sys[w >> 22];
-            Thermo3 th{0.f, 0.f, 0.f};
+            Thermo3 th{0.0, 0.0, 0.0};
             force_tile<B, false, VAR>(d, (int)(w & 0x3fffffu), flags, smem, th);
             __syncthreads();
             thermo_flush(d, th, (double *)(smem + TilePlan<B>::red_off()));

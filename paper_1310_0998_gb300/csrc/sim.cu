@@ -110,19 +110,19 @@ template <int B>
 __global__ void k_kick_bin(Sys d)
 {
     __shared__ double s_red[3 * 33];
-    Thermo3 th{0.f, 0.f, 0.f};
+    Thermo3 th{0.0, 0.0, 0.0};
     // grid-stride over the beads with a capped grid: the per-block FP64 thermo
     // flush targets one address, and one flush per 256 beads serialised there
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
         const uint4 xv = d.C_xv[k];
         const float2 f = d.C_f[k];
         float vx = vbits(xv.z), vy = vbits(xv.w);
-        th.ke += vx * vx + vy * vy;
-        th.px += vx;
-        th.py += vy;
-        vx += d.hdtm * f.x;
-        vy += d.hdtm * f.y;
-        const float ddx = d.dt * vx, ddy = d.dt * vy;
+        th.ke = fma((double)vx, (double)vx, fma((double)vy, (double)vy, th.ke));
+        th.px += (double)vx;
+        th.py += (double)vy;
+        vx = __fmaf_rn(d.hdtm, f.x, vx);
+        vy = __fmaf_rn(d.hdtm, f.y, vy);
+        const float ddx = __fmul_rn(d.dt, vx), ddy = __fmul_rn(d.dt, vy);
         uint32_t nx = xv.x, ny = xv.y;
         if (fabsf(ddx) < 0.25f * d.L && fabsf(ddy) < 0.25f * d.L) {
             nx = fx_add(d, xv.x, ddx);
@@ -143,7 +143,7 @@ template <int B, bool COUNT, int VAR>
 __global__ void __launch_bounds__(TILE_THREADS, 10) k_force(Sys d, int flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    Thermo3 th{0.f, 0.f, 0.f};
+    Thermo3 th{0.0, 0.0, 0.0};
     force_tile<B, COUNT, VAR>(d, blockIdx.x, flags, smem, th);
     if (flags & (F_ADVANCE | F_FINAL)) {
         __syncthreads();
@@ -229,6 +229,10 @@ void fill_physics(Sys &d, const dpd_params *p)
     const double s = p->wexp > 0.0 ? p->wexp : 2.0;
     d.gen_w = s != 2.0 ? 1 : 0;
     d.hwexp = (float)(0.5 * s);
+    // pair geometry in fixed-point units (needs the geometry's unit length)
+    const double rcu = p->rc / std::ldexp(p->L, -32);
+    d.rc2u = (float)(rcu * rcu);
+    d.inv_rcu = (float)(std::ldexp(p->L, -32) / p->rc);
 }
 
 void fill_geometry(Sys &d, const dpd_params *p, int B)
@@ -508,7 +512,7 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     d.cap = tile_capacity(p, c->B);
     c->smem = force_smem(c->B, c->var, d.cap, false);
     if (force_smem(c->B, c->var, d.cap, true) > 200 * 1024) {
-        d.cap = (int)((200 * 1024 - force_smem(c->B, c->var, 0, true)) / 35) & ~31;
+        d.cap = (int)((200 * 1024 - force_smem(c->B, c->var, 0, true)) / (c->var == 3 ? 43 : 41)) & ~31;
         c->smem = force_smem(c->B, c->var, d.cap, false);
     }
     c->nscan = (d.ncells + SCAN_TILE - 1) / SCAN_TILE;

@@ -187,11 +187,32 @@ __device__ __forceinline__ void bin_one(const Sys &d, int k)
 }
 
 // ------------------------------------------------------------- integrate ----
-struct Thermo3 { float ke, px, py; };
+// Thermo partials of one thread, FP64: sum |v|^2, sum v_x, sum v_y.
+struct Thermo3 { double ke, px, py; };
+
+// Pair forces are summed per bead as 64-bit fixed point, 2^-32 force units per
+// count.  Integer addition is associative, so a bead's force does not depend on
+// the order in which its pairs are met (the in-cell order of the counting sort
+// comes from atomic tickets and varies from run to run); every FP32 pair
+// contribution of magnitude 2^-9 or more converts exactly.  A pair force of
+// magnitude FQ_MAX or more (a blown-up state) is reported as non-finite.
+constexpr float FQ_SCALE = 4294967296.0f;            // 2^32
+constexpr float FQ_INV = 2.3283064365386963e-10f;    // 2^-32
+constexpr float FQ_MAX = 1.0e8f;
+__device__ __forceinline__ long long fq(float g) { return __float2ll_rn(__fmul_rn(g, FQ_SCALE)); }
+__device__ __forceinline__ float fq_to_f(long long q) { return __fmul_rn(__ll2float_rn(q), FQ_INV); }
+__device__ __forceinline__ void fq_add(long long *a, long long q)
+{
+    atomicAdd((unsigned long long *)a, (unsigned long long)q);
+}
 
 // Everything after the pair sum for one owned bead at sorted slot g:
 // bond + propulsion (partner through slot[id ^ 1]), drag, the two half kicks
 // and the drift, canonical output, binning of the new position.
+// Every floating-point operation of the step is written with an explicit
+// rounding (fused where a fused multiply-add is meant), so that the kernels
+// that inline this code, whose flags the compiler may or may not know, all
+// produce the same bits.
 template <int B>
 __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, uint32_t id, float fx, float fy,
                                                int flags, Thermo3 &th)
@@ -201,34 +222,37 @@ __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, ui
         const uint4 xp = d.S_xv[ps];
         const float dx = mdiff(d, xv.x, xp.x);
         const float dy = mdiff(d, xv.y, xp.y);
-        const float r2 = dx * dx + dy * dy;
+        const float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
         if (r2 > 0.f) {
-            const float r = sqrtf(r2);
-            const float inv = 1.0f / r;
-            const float ex = dx * inv, ey = dy * inv;   // from partner to self
-            const float fb = -d.kbond * (r - d.r0);
-            const float sp = (id & 1u) ? -d.fp : d.fp;  // n_k = head - tail
-            fx += (fb + sp) * ex;
-            fy += (fb + sp) * ey;
+            const float r = __fsqrt_rn(r2);
+            const float inv = __fdiv_rn(1.0f, r);
+            const float ex = __fmul_rn(dx, inv), ey = __fmul_rn(dy, inv);   // from partner to self
+            const float fb = __fmul_rn(-d.kbond, __fsub_rn(r, d.r0));
+            const float sp = (id & 1u) ? -d.fp : d.fp;                        // n_k = head - tail
+            fx = __fmaf_rn(__fadd_rn(fb, sp), ex, fx);
+            fy = __fmaf_rn(__fadd_rn(fb, sp), ey, fy);
         }
     } else {
         set_err_at(d, ERR_INTERNAL, 2, g, id, ps);
     }
     float vx = vbits(xv.z), vy = vbits(xv.w);
-    fx -= d.zeta * vx;
-    fy -= d.zeta * vy;
-    if (!(flags & F_FIRST)) { vx += d.hdtm * fx; vy += d.hdtm * fy; }
-    th.ke += vx * vx + vy * vy;
-    th.px += vx;
-    th.py += vy;
+    fx = __fmaf_rn(-d.zeta, vx, fx);
+    fy = __fmaf_rn(-d.zeta, vy, fy);
+    if (!(flags & F_FIRST)) { vx = __fmaf_rn(d.hdtm, fx, vx); vy = __fmaf_rn(d.hdtm, fy, vy); }
+    {
+        const double dvx = (double)vx, dvy = (double)vy;
+        th.ke = fma(dvx, dvx, fma(dvy, dvy, th.ke));
+        th.px += dvx;
+        th.py += dvy;
+    }
     if (flags & F_FINAL) {
         d.C_xv[id] = make_uint4(xv.x, xv.y, fbits(vx), fbits(vy));
         d.C_f[id] = make_float2(fx, fy);
     }
     if (flags & F_ADVANCE) {
-        vx += d.hdtm * fx;
-        vy += d.hdtm * fy;
-        const float ddx = d.dt * vx, ddy = d.dt * vy;
+        vx = __fmaf_rn(d.hdtm, fx, vx);
+        vy = __fmaf_rn(d.hdtm, fy, vy);
+        const float ddx = __fmul_rn(d.dt, vx), ddy = __fmul_rn(d.dt, vy);
         uint32_t nx = xv.x, ny = xv.y;
         if (fabsf(ddx) < 0.25f * d.L && fabsf(ddy) < 0.25f * d.L) {   // false for NaN too
             nx = fx_add(d, xv.x, ddx);
@@ -244,6 +268,52 @@ __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, ui
     }
 }
 
+// ------------------------------------------------------------- pair force ----
+// Pair separation in fixed-point units: the exact integer difference of the
+// two coordinates, one rounding to FP32.  Negating the pair negates it
+// exactly, so a pair evaluated from either bead (or by either of two tiles)
+// gives exactly opposite forces, and the range test is the same decision from
+// both sides.
+__device__ __forceinline__ float sep_u(uint32_t a, uint32_t b) { return (float)(int)(a - b); }
+__device__ __forceinline__ float r2_u(float ux, float uy) { return __fmaf_rn(ux, ux, __fmul_rn(uy, uy)); }
+__device__ __forceinline__ bool in_range(const Sys &d, float r2u) { return (r2u < d.rc2u) & (r2u > 0.f); }
+
+// Scalar F of the pair force F e_ij (Eqs. DPDf, DPDcdr, weightFunc01):
+// F = w [a - gamma w (v_ij . e_ij) + sigma alpha_ij / sqrt(dt)], w = 1 - r / r_c,
+// e_ij = (x_i - x_j) / r; returns F and e_ij.  Written with explicit roundings
+// (no contraction left to the compiler) so that every kernel that inlines it
+// produces the same bits.
+__device__ __forceinline__ float dpd_pair_scalar(const Sys &d, float ux, float uy, float r2u, float dvx, float dvy,
+                                                 uint32_t idi, uint32_t idj, uint32_t s_lo, uint32_t s_hi,
+                                                 float &ex, float &ey)
+{
+    const float rinv = rsqrtf(r2u);
+    const float w = __fmaf_rn(-__fmul_rn(r2u, rinv), d.inv_rcu, 1.0f);
+    ex = __fmul_rn(ux, rinv);
+    ey = __fmul_rn(uy, rinv);
+    const float dve = __fmaf_rn(dvx, ex, __fmul_rn(dvy, ey));
+    const float nz = pair_noise(d, idi, idj, s_lo, s_hi);
+    if (!d.gen_w)
+        return __fmul_rn(w, __fmaf_rn(d.sig_r, nz, __fmaf_rn(-__fmul_rn(d.gamma, w), dve, d.a)));
+    // changed exponent of w: w_R = w^(s/2), w_D = w_R^2 (uniform branch)
+    const float wr = __powf(w, d.hwexp);
+    return __fmaf_rn(d.a, w, __fmaf_rn(-__fmul_rn(d.gamma, __fmul_rn(wr, wr)), dve,
+                                       __fmul_rn(__fmul_rn(d.sig_r, wr), nz)));
+}
+
+// Force of the pair (i, j) on i as fixed-point counts; flags a blown-up pair.
+__device__ __forceinline__ void pair_force_q(const Sys &d, uint2 xi, uint2 xj, float2 vi, float2 vj, uint32_t idi,
+                                             uint32_t idj, uint32_t s_lo, uint32_t s_hi, long long &qx, long long &qy)
+{
+    const float ux = sep_u(xi.x, xj.x), uy = sep_u(xi.y, xj.y);
+    float ex, ey;
+    const float F = dpd_pair_scalar(d, ux, uy, r2_u(ux, uy), __fsub_rn(vi.x, vj.x), __fsub_rn(vi.y, vj.y), idi, idj,
+                                    s_lo, s_hi, ex, ey);
+    if (!(fabsf(F) < FQ_MAX)) set_err(d, ERR_NONFINITE);
+    qx = fq(__fmul_rn(F, ex));
+    qy = fq(__fmul_rn(F, ey));
+}
+
 // ------------------------------------------------------------ force tile ----
 // Shared-memory plan of one tile (B x B owned cells + one-cell halo).
 constexpr int TILE_THREADS = 128;
@@ -251,14 +321,15 @@ template <int B>
 struct TilePlan {
     static constexpr int NCL = (B + 2) * (B + 2);   // local cell table
     static constexpr int NH = 4 * B + 4;            // halo cells
-    static constexpr int NINT = 2 * NCL + 5 * (NH + 1) + 2 * (B + 2) + 8;
+    static constexpr int NINT = 2 * NCL + 3 * (NH + 1) + 8;
     static __host__ __device__ size_t red_off() { return ((size_t)NINT * 4 + 7) & ~size_t(7); }
     static __host__ __device__ size_t bead_off(int nthreads)
     {
         return (red_off() + sizeof(double) * 3 * (size_t)(nthreads / 32 + 1) + 15) & ~size_t(15);
     }
-    // per staged bead: pos 8, vel 8, id 4, fx 4, fy 4, local cell 1 (+ count 4)
-    static __host__ __device__ size_t bead_bytes(bool count) { return count ? 33 : 29; }
+    // per staged bead: position 8, velocity 8, force counts 16, id 4,
+    // local cell 1 (+ count 4)
+    static __host__ __device__ size_t bead_bytes(bool count) { return count ? 41 : 37; }
     static __host__ __device__ size_t queue_off(int cap, int nthreads, bool count)
     {
         return (bead_off(nthreads) + (size_t)cap * bead_bytes(count) + 15) & ~size_t(15);
@@ -269,23 +340,30 @@ struct TilePlan {
     }
 };
 
-__device__ __forceinline__ float dpd_pair_scalar(const Sys &d, float dx, float dy, float dvx, float dvy,
-                                                 uint32_t idi, uint32_t idj, uint32_t s_lo, uint32_t s_hi,
-                                                 float r2, float &ex, float &ey)
-{
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float w = 1.0f - r * d.inv_rc;
-    ex = dx * rinv;
-    ey = dy * rinv;
-    const float dve = dvx * ex + dvy * ey;
-    const float nz = pair_noise(d, idi, idj, s_lo, s_hi);
-    if (!d.gen_w) return w * (d.a - d.gamma * w * dve + d.sig_r * nz);
-    // changed exponent of w: w_R = w^(s/2), w_D = w_R^2 (uniform branch)
-    const float wr = __powf(w, d.hwexp);
-    return d.a * w - d.gamma * (wr * wr) * dve + d.sig_r * wr * nz;
-}
+// Shared arrays of a staged tile (variants 1 and 2): cap beads, cap a multiple
+// of 32 so every array starts 16-byte aligned.
+struct TileArrays {
+    uint2 *X;          // fixed-point position
+    float2 *v;         // velocity
+    long long *f;      // force counts (x, y) of the pairs met so far
+    uint32_t *id;
+    uint32_t *cnt;     // interacting neighbours (COUNT only)
+    unsigned char *lc; // local cell (lx | ly << 4) of an owned bead
+};
 
+template <int B>
+__device__ __forceinline__ TileArrays tile_arrays(unsigned char *smem, int cap, int nthreads, bool count)
+{
+    TileArrays a;
+    unsigned char *p = smem + TilePlan<B>::bead_off(nthreads);
+    a.X = (uint2 *)p;
+    a.v = (float2 *)(p + 8 * (size_t)cap);
+    a.f = (long long *)(p + 16 * (size_t)cap);
+    a.id = (uint32_t *)(p + 32 * (size_t)cap);
+    a.cnt = (uint32_t *)(p + 36 * (size_t)cap);
+    a.lc = p + (count ? 40 : 36) * (size_t)cap;
+    return a;
+}
 
 // Neighbour offsets packed 2 bits per entry (value + 1), entries in the
 // order 0 = own cell, 1-4 ahead (E, NE, N, NW), 5-8 behind (W, SW, S, SE).
@@ -294,26 +372,19 @@ constexpr uint32_t NB_DX = 0x1u | (2u << 2) | (2u << 4) | (1u << 6) | (0u << 8) 
 constexpr uint32_t NB_DY = 0x1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8) | (1u << 10) | (0u << 12) |
                            (0u << 14) | (0u << 16);
 
-// Offset of bead i seen from a bead in the cell (dx, dy) away.
-__device__ __forceinline__ float shift_off(float o, int dx, float cs)
-{
-    return dx == 0 ? o : (dx > 0 ? o - cs : o + cs);
-}
-
 // Variant 1: one thread per owned bead walks its candidates and evaluates
 // each interacting pair in place (divergent; kept as the simple reference
-// kernel and for the autotuner).
+// kernel and as an alternative for the autotuner).
 template <int B, bool COUNT>
 __device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, int th_, const int *s_cbeg,
-                                             const int *s_ccnt, const float2 *s_pos, const float2 *s_vel,
-                                             const uint32_t *s_id, float *s_fx, float *s_fy, uint32_t *s_cnt,
-                                             const unsigned char *s_lc, uint32_t s_lo, uint32_t s_hi)
+                                             const int *s_ccnt, const TileArrays &t, uint32_t s_lo, uint32_t s_hi)
 {
     for (int k = threadIdx.x; k < n_own; k += blockDim.x) {
-        const float2 oi = s_pos[k], vi = s_vel[k];
-        const uint32_t idi = s_id[k], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
-        const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
-        float fx = 0.f, fy = 0.f;
+        const uint2 xi = t.X[k];
+        const float2 vi = t.v[k];
+        const uint32_t idi = t.id[k], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
+        const int lx = t.lc[k] & 15, ly = t.lc[k] >> 4;
+        long long fx = 0, fy = 0;
         uint32_t cnt = 0;
 #pragma unroll 1
         for (int nb = 0; nb < 9; ++nb) {
@@ -321,87 +392,92 @@ __device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, in
             const int nlx = lx + ox_, nly = ly + oy_;
             const bool owned = (nlx >= 0 && nlx < tw && nly >= 0 && nly < th_);
             if (nb >= 5 && owned) continue;    // the other bead's forward sweep takes it
-            const bool newton = owned;
-            const float pix = shift_off(oi.x, ox_, d.cs), piy = shift_off(oi.y, oy_, d.cs);
             const int lc = (nly + 1) * (B + 2) + nlx + 1;
             int j = s_cbeg[lc];
             const int je = j + s_ccnt[lc];
             if (nb == 0) j = k + 1;
             for (; j < je; ++j) {
-                const float2 pj = s_pos[j];
-                const float dx = pix - pj.x, dy = piy - pj.y;
-                const float r2 = dx * dx + dy * dy;
-                if (r2 < d.rc2 && r2 > 0.f) {
-                    const uint32_t idj = s_id[j];
-                    if (idj == pid) continue;
-                    const float2 vj = s_vel[j];
-                    float ex, ey;
-                    const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, idi, idj, s_lo, s_hi, r2,
-                                                    ex, ey);
-                    fx += F * ex;
-                    fy += F * ey;
-                    if (COUNT) ++cnt;
-                    if (newton) {
-                        atomicAdd(&s_fx[j], -F * ex);
-                        atomicAdd(&s_fy[j], -F * ey);
-                        if (COUNT) atomicAdd(&s_cnt[j], 1u);
-                    }
+                const uint2 xj = t.X[j];
+                if (!in_range(d, r2_u(sep_u(xi.x, xj.x), sep_u(xi.y, xj.y)))) continue;
+                const uint32_t idj = t.id[j];
+                if (idj == pid) continue;
+                long long qx, qy;
+                pair_force_q(d, xi, xj, vi, t.v[j], idi, idj, s_lo, s_hi, qx, qy);
+                fx += qx;
+                fy += qy;
+                if (COUNT) ++cnt;
+                if (owned) {
+                    fq_add(&t.f[2 * j], -qx);
+                    fq_add(&t.f[2 * j + 1], -qy);
+                    if (COUNT) atomicAdd(&t.cnt[j], 1u);
                 }
             }
         }
-        atomicAdd(&s_fx[k], fx);
-        atomicAdd(&s_fy[k], fy);
-        if (COUNT) atomicAdd(&s_cnt[k], cnt);
+        fq_add(&t.f[2 * k], fx);
+        fq_add(&t.f[2 * k + 1], fy);
+        if (COUNT) atomicAdd(&t.cnt[k], cnt);
     }
 }
 
 // Variant 2: pair queue.  Each lane walks the candidates of one owned bead at
 // a time (taking the next bead from a block-wide counter when it runs out, so
 // warps stay balanced); every candidate inside r_c is pushed, packed as
-// (i, j, Newton-3 flag, cell offset), into the warp's 128-entry buffer.
-// Whenever 32 pairs are queued the whole warp evaluates them together, so
-// the Philox and force arithmetic runs with every lane active.  Forces land
-// in shared memory through atomics on both sides of a Newton-3 pair.
+// (i, j, Newton-3 flag), into the warp's 128-entry buffer.  Whenever 32 pairs
+// are queued the whole warp evaluates them together, so the Philox and force
+// arithmetic runs with every lane active.  Forces land in shared memory
+// through fixed-point atomics on both sides of a Newton-3 pair.
 template <bool COUNT>
-__device__ __forceinline__ void queue_eval(const Sys &d, uint32_t code, const float2 *s_pos, const float2 *s_vel,
-                                           const uint32_t *s_id, float *s_fx, float *s_fy, uint32_t *s_cnt,
-                                           uint32_t s_lo, uint32_t s_hi)
+__device__ __forceinline__ void queue_eval(const Sys &d, uint32_t code, const TileArrays &t, uint32_t s_lo,
+                                           uint32_t s_hi)
 {
     const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
-    const bool newton = (code >> 24) & 1u;
-    const int dcx = (int)((code >> 25) & 3u) - 1, dcy = (int)((code >> 27) & 3u) - 1;
-    const float2 oi = s_pos[k], pj = s_pos[j], vi = s_vel[k], vj = s_vel[j];
-    const float dx = shift_off(oi.x, dcx, d.cs) - pj.x, dy = shift_off(oi.y, dcy, d.cs) - pj.y;
-    const float r2 = dx * dx + dy * dy;
-    float ex, ey;
-    const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, s_id[k], s_id[j], s_lo, s_hi, r2, ex, ey);
-    const float gx = F * ex, gy = F * ey;
-    atomicAdd(&s_fx[k], gx);
-    atomicAdd(&s_fy[k], gy);
-    if (COUNT) atomicAdd(&s_cnt[k], 1u);
-    if (newton) {
-        atomicAdd(&s_fx[j], -gx);
-        atomicAdd(&s_fy[j], -gy);
-        if (COUNT) atomicAdd(&s_cnt[j], 1u);
+    long long qx, qy;
+    pair_force_q(d, t.X[k], t.X[j], t.v[k], t.v[j], t.id[k], t.id[j], s_lo, s_hi, qx, qy);
+    fq_add(&t.f[2 * k], qx);
+    fq_add(&t.f[2 * k + 1], qy);
+    if (COUNT) atomicAdd(&t.cnt[k], 1u);
+    if ((code >> 24) & 1u) {
+        fq_add(&t.f[2 * j], -qx);
+        fq_add(&t.f[2 * j + 1], -qy);
+        if (COUNT) atomicAdd(&t.cnt[j], 1u);
+    }
+}
+
+// Evaluate the oldest 32 entries of a warp queue of qn >= 32 entries (NQ
+// entries of capacity beyond the first 32) and move the rest to the front.
+template <int NQ, typename EVAL>
+__device__ __forceinline__ void queue_drain(volatile uint32_t *q, int &qn, EVAL eval)
+{
+    const int lane = threadIdx.x & 31;
+    while (qn >= 32) {
+        const uint32_t mine = q[lane];
+        uint32_t carry[NQ];
+#pragma unroll
+        for (int u = 0; u < NQ; ++u) carry[u] = q[32 * (u + 1) + lane];
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < NQ; ++u)
+            if (lane + 32 * u < qn - 32) q[lane + 32 * u] = carry[u];
+        qn -= 32;
+        __syncwarp();
+        eval(mine);
     }
 }
 
 template <int B, bool COUNT>
 __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int th_, const int *s_cbeg,
-                                            const int *s_ccnt, const float2 *s_pos, const float2 *s_vel,
-                                            const uint32_t *s_id, float *s_fx, float *s_fy, uint32_t *s_cnt,
-                                            const unsigned char *s_lc, volatile uint32_t *q, int *s_next,
-                                            uint32_t s_lo, uint32_t s_hi)
+                                            const int *s_ccnt, const TileArrays &t, volatile uint32_t *q,
+                                            int *s_next, uint32_t s_lo, uint32_t s_hi)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int k = -1, j = 0, je = 0, lc0 = 0;
     uint32_t visit = 0, own = 0, pid = 0, tag = 0;
-    float2 oi = make_float2(0.f, 0.f);
-    float pix = 0.f, piy = 0.f;
+    uint2 xi = make_uint2(0u, 0u);
     bool more = true;
     int qn = 0;   // warp-uniform queue length (entries q[0, qn))
+    auto eval = [&](uint32_t code) { queue_eval<COUNT>(d, code, t, s_lo, s_hi); };
     while (true) {
         // At most one advance per lane per round (to the next neighbour
         // range of its bead, or to its next bead), so a lane switching cells
@@ -413,10 +489,10 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
                 if (k >= n_own) {
                     more = false;
                 } else {
-                    oi = s_pos[k];
-                    const int lx = s_lc[k] & 15, ly = s_lc[k] >> 4;
+                    xi = t.X[k];
+                    const int lx = t.lc[k] & 15, ly = t.lc[k] >> 4;
                     lc0 = (ly + 1) * (B + 2) + lx + 1;
-                    pid = d.excl ? (s_id[k] ^ 1u) : 0xffffffffu;
+                    pid = d.excl ? (t.id[k] ^ 1u) : 0xffffffffu;
                     // which neighbour cells are owned by this tile (Newton-3 side)
                     const uint32_t px = lx < tw - 1, nx = lx > 0, py = ly < th_ - 1, ny = ly > 0;
                     own = 1u | (px << 1) | ((px & py) << 2) | (py << 3) | ((nx & py) << 4) | (nx << 5) |
@@ -432,10 +508,7 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
                 j = s_cbeg[lc];
                 je = j + s_ccnt[lc];
                 if (nb == 0) j = k + 1;
-                pix = shift_off(oi.x, ox_, d.cs);
-                piy = shift_off(oi.y, oy_, d.cs);
-                tag = (uint32_t)k | (((own >> nb) & 1u) << 24) | ((uint32_t)(ox_ + 1) << 25) |
-                      ((uint32_t)(oy_ + 1) << 27);
+                tag = (uint32_t)k | (((own >> nb) & 1u) << 24);
                 have = j < je;
             }
         }
@@ -445,17 +518,13 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
         bool p0 = false, p1 = false;
         uint32_t c0 = 0, c1 = 0;
         if (have) {
-            const float2 pj = s_pos[j];
-            const float dx = pix - pj.x, dy = piy - pj.y;
-            const float r2 = dx * dx + dy * dy;
-            p0 = (r2 < d.rc2) & (r2 > 0.f) & (s_id[j] != pid);
+            const uint2 xj = t.X[j];
+            p0 = in_range(d, r2_u(sep_u(xi.x, xj.x), sep_u(xi.y, xj.y))) & (t.id[j] != pid);
             c0 = tag | ((uint32_t)j << 12);
             ++j;
             if (j < je) {
-                const float2 pk = s_pos[j];
-                const float ex = pix - pk.x, ey = piy - pk.y;
-                const float s2 = ex * ex + ey * ey;
-                p1 = (s2 < d.rc2) & (s2 > 0.f) & (s_id[j] != pid);
+                const uint2 xk = t.X[j];
+                p1 = in_range(d, r2_u(sep_u(xi.x, xk.x), sep_u(xi.y, xk.y))) & (t.id[j] != pid);
                 c1 = tag | ((uint32_t)j << 12);
                 ++j;
             }
@@ -467,24 +536,15 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
         if (p1) q[qn + n0 + __popc(m1 & lt)] = c1;
         qn += n0 + __popc(m1);
         __syncwarp();
-        while (qn >= 32) {
-            // evaluate the oldest 32 entries, move the rest to the front
-            const uint32_t mine = q[lane];
-            const uint32_t carry0 = q[32 + lane], carry1 = q[64 + lane];
-            __syncwarp();
-            if (lane < qn - 32) q[lane] = carry0;
-            if (lane + 32 < qn - 32) q[lane + 32] = carry1;
-            qn -= 32;
-            __syncwarp();
-            queue_eval<COUNT>(d, mine, s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lo, s_hi);
-        }
+        queue_drain<2>(q, qn, eval);
     }
     __syncwarp();
-    if (lane < qn) queue_eval<COUNT>(d, q[lane], s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lo, s_hi);
+    if (lane < qn) eval(q[lane]);
 }
 
 // Global-memory path for a tile whose beads do not fit in shared memory: one
-// thread per owned bead, pairs from both sides (no Newton-3), same arithmetic.
+// thread per owned bead, pairs from both sides (no Newton-3), the same pair
+// arithmetic and fixed-point sums, hence the same bits as the shared path.
 template <int B, bool COUNT>
 __device__ void force_tile_global(const Sys &d, uint32_t g0, int n_own, uint32_t s_lo, uint32_t s_hi, int flags,
                                   Thermo3 &th)
@@ -495,10 +555,11 @@ __device__ void force_tile_global(const Sys &d, uint32_t g0, int n_own, uint32_t
     for (int k = tid; k < n_own; k += NT) {
         const int g = (int)g0 + k;
         const uint4 xv = d.S_xv[g];
-        const float vix = vbits(xv.z), viy = vbits(xv.w);
+        const uint2 xi = make_uint2(xv.x, xv.y);
+        const float2 vi = make_float2(vbits(xv.z), vbits(xv.w));
         const uint32_t idi = d.S_id[g], pid = d.excl ? (idi ^ 1u) : 0xffffffffu;
         const int cx = cell_coord(d, xv.x), cy = cell_coord(d, xv.y);
-        float fx = 0.f, fy = 0.f;
+        long long fx = 0, fy = 0;
         uint32_t cnt = 0;
         for (int oy_ = -1; oy_ <= 1; ++oy_)
             for (int ox_ = -1; ox_ <= 1; ++ox_) {
@@ -512,35 +573,29 @@ __device__ void force_tile_global(const Sys &d, uint32_t g0, int n_own, uint32_t
                     const uint32_t idj = d.S_id[q];
                     if (idj == pid) continue;
                     const uint4 xj = d.S_xv[q];
-                    const float dx = mdiff(d, xv.x, xj.x);
-                    const float dy = mdiff(d, xv.y, xj.y);
-                    const float r2 = dx * dx + dy * dy;
-                    if (r2 < d.rc2 && r2 > 0.f) {
-                        float ex, ey;
-                        const float F = dpd_pair_scalar(d, dx, dy, vix - vbits(xj.z), viy - vbits(xj.w), idi,
-                                                        idj, s_lo, s_hi, r2, ex, ey);
-                        fx += F * ex;
-                        fy += F * ey;
-                        if (COUNT) ++cnt;
-                    }
+                    if (!in_range(d, r2_u(sep_u(xv.x, xj.x), sep_u(xv.y, xj.y)))) continue;
+                    long long qx, qy;
+                    pair_force_q(d, xi, make_uint2(xj.x, xj.y), vi, make_float2(vbits(xj.z), vbits(xj.w)), idi, idj,
+                                 s_lo, s_hi, qx, qy);
+                    fx += qx;
+                    fy += qy;
+                    if (COUNT) ++cnt;
                 }
             }
         if (COUNT && d.pcnt) d.pcnt[idi] = cnt;
-        integrate_bead<B>(d, g, xv, idi, fx, fy, flags, th);
+        integrate_bead<B>(d, g, xv, idi, fq_to_f(fx), fq_to_f(fy), flags, th);
     }
 }
 
 // ------------------------------------------------- grid-order tile (VAR 3) --
 // The tile's owned and halo cells are staged in shared memory in the row-major
-// order of the local (B+2) x (B+2) cell grid, with raw fixed-point positions,
-// so every row of the local grid is one contiguous bead range and a pair
-// separation is the wrapped integer difference of two positions (exact) times
-// the unit.  The forward half-stencil of an owned cell (own cell after the
-// bead, E, and NW..NE) is then two ranges instead of five; a cell on the tile
-// edge adds at most three ranges of halo cells behind it (W, and SW..SE or
-// parts of that row).  Each lane walks the candidates of one owned bead at a
-// time, CPR candidates per round; pairs inside r_c go through the warp's pair
-// queue as in variant 2 (Newton-3 when the partner is owned).
+// order of the local (B+2) x (B+2) cell grid, so every row of the local grid is
+// one contiguous bead range.  The forward half-stencil of an owned cell (own
+// cell after the bead, E, and NW..NE) is then two ranges instead of five; a
+// cell on the tile edge adds at most three ranges of halo cells behind it (W,
+// and SW..SE or parts of that row).  Each lane walks the candidates of one
+// owned bead at a time, CPR candidates per round; pairs inside r_c go through
+// the warp's pair queue as in variant 2 (Newton-3 when the partner is owned).
 template <int B>
 struct TilePlanG {
     static constexpr int W = B + 2;
@@ -553,9 +608,9 @@ struct TilePlanG {
     {
         return (red_off() + sizeof(double) * 3 * (size_t)(nthreads / 32 + 1) + 15) & ~size_t(15);
     }
-    // per staged bead: position 8, velocity 8, id 4, fx 4, fy 4, (count 4),
-    // owned-bead slot 2, owned flag 1
-    static __host__ __device__ size_t bead_bytes(bool count) { return count ? 35 : 31; }
+    // per staged bead: position 8, velocity 8, force counts 16, id 4,
+    // (count 4), owned-bead slot 2, owned flag 1
+    static __host__ __device__ size_t bead_bytes(bool count) { return count ? 43 : 39; }
     static __host__ __device__ size_t queue_off(int cap, int nthreads, bool count)
     {
         return (bead_off(nthreads) + (size_t)cap * bead_bytes(count) + 15) & ~size_t(15);
@@ -567,34 +622,26 @@ struct TilePlanG {
 };
 
 template <bool COUNT>
-__device__ __forceinline__ void queue_eval_g(const Sys &d, uint32_t code, const uint2 *s_X, const float2 *s_vel,
-                                             const uint32_t *s_id, const unsigned char *s_own, float *s_fx,
-                                             float *s_fy, uint32_t *s_cnt, uint32_t s_lo, uint32_t s_hi)
+__device__ __forceinline__ void queue_eval_g(const Sys &d, uint32_t code, const TileArrays &t,
+                                             const unsigned char *s_own, uint32_t s_lo, uint32_t s_hi)
 {
     const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
-    const uint2 xi = s_X[k], xj = s_X[j];
-    const float2 vi = s_vel[k], vj = s_vel[j];
-    const float dx = mdiff(d, xi.x, xj.x), dy = mdiff(d, xi.y, xj.y);
-    const float r2 = dx * dx + dy * dy;
-    float ex, ey;
-    const float F = dpd_pair_scalar(d, dx, dy, vi.x - vj.x, vi.y - vj.y, s_id[k], s_id[j], s_lo, s_hi, r2, ex, ey);
-    const float gx = F * ex, gy = F * ey;
-    atomicAdd(&s_fx[k], gx);
-    atomicAdd(&s_fy[k], gy);
-    if (COUNT) atomicAdd(&s_cnt[k], 1u);
+    long long qx, qy;
+    pair_force_q(d, t.X[k], t.X[j], t.v[k], t.v[j], t.id[k], t.id[j], s_lo, s_hi, qx, qy);
+    fq_add(&t.f[2 * k], qx);
+    fq_add(&t.f[2 * k + 1], qy);
+    if (COUNT) atomicAdd(&t.cnt[k], 1u);
     if (s_own[j]) {
-        atomicAdd(&s_fx[j], -gx);
-        atomicAdd(&s_fy[j], -gy);
-        if (COUNT) atomicAdd(&s_cnt[j], 1u);
+        fq_add(&t.f[2 * j], -qx);
+        fq_add(&t.f[2 * j + 1], -qy);
+        if (COUNT) atomicAdd(&t.cnt[j], 1u);
     }
 }
 
 template <int B, bool COUNT>
 __device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int y0, int tw, const int *s_lbeg,
-                                           const uint2 *s_X, const float2 *s_vel, const uint32_t *s_id,
-                                           const unsigned char *s_own, const uint16_t *s_oslot, float *s_fx,
-                                           float *s_fy, uint32_t *s_cnt, volatile uint32_t *q, int *s_next,
-                                           uint32_t s_lo, uint32_t s_hi)
+                                           const TileArrays &t, const unsigned char *s_own, const uint16_t *s_oslot,
+                                           volatile uint32_t *q, int *s_next, uint32_t s_lo, uint32_t s_hi)
 {
     using TP = TilePlanG<B>;
     constexpr int W = TP::W, CPR = TP::CPR;
@@ -605,6 +652,7 @@ __device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int 
     uint32_t Xi = 0, Yi = 0, pid = 0;
     bool more = true;
     int qn = 0;   // warp-uniform queue length
+    auto eval = [&](uint32_t code) { queue_eval_g<COUNT>(d, code, t, s_own, s_lo, s_hi); };
     while (true) {
         bool have = j < je;
         if (!have && more) {
@@ -614,10 +662,10 @@ __device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int 
                     more = false;
                 } else {
                     si = s_oslot[k];
-                    const uint2 x = s_X[si];
+                    const uint2 x = t.X[si];
                     Xi = x.x;
                     Yi = x.y;
-                    pid = d.excl ? (s_id[si] ^ 1u) : 0xffffffffu;
+                    pid = d.excl ? (t.id[si] ^ 1u) : 0xffffffffu;
                     lx = cell_coord(d, Xi) - x0;
                     ly = cell_coord(d, Yi) - y0;
                     lx += lx < -1 ? d.nc : 0;   // a tile never spans the box, so one wrap at most
@@ -657,10 +705,8 @@ __device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int 
             p[u] = false;
             c[u] = 0u;
             if (j < je) {
-                const uint2 xj = s_X[j];
-                const float dx = mdiff(d, Xi, xj.x), dy = mdiff(d, Yi, xj.y);
-                const float r2 = dx * dx + dy * dy;
-                p[u] = (r2 < d.rc2) & (r2 > 0.f) & (s_id[j] != pid);
+                const uint2 xj = t.X[j];
+                p[u] = in_range(d, r2_u(sep_u(Xi, xj.x), sep_u(Yi, xj.y))) & (t.id[j] != pid);
                 c[u] = (uint32_t)si | ((uint32_t)j << 12);
                 ++j;
             }
@@ -672,23 +718,10 @@ __device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int 
             qn += __popc(m);
         }
         __syncwarp();
-        while (qn >= 32) {
-            // evaluate the oldest 32 entries, move the rest (< 32 CPR) to the front
-            const uint32_t mine = q[lane];
-            uint32_t carry[CPR];
-#pragma unroll
-            for (int u = 0; u < CPR; ++u) carry[u] = q[32 * (u + 1) + lane];
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < CPR; ++u)
-                if (lane + 32 * u < qn - 32) q[lane + 32 * u] = carry[u];
-            qn -= 32;
-            __syncwarp();
-            queue_eval_g<COUNT>(d, mine, s_X, s_vel, s_id, s_own, s_fx, s_fy, s_cnt, s_lo, s_hi);
-        }
+        queue_drain<CPR>(q, qn, eval);
     }
     __syncwarp();
-    if (lane < qn) queue_eval_g<COUNT>(d, q[lane], s_X, s_vel, s_id, s_own, s_fx, s_fy, s_cnt, s_lo, s_hi);
+    if (lane < qn) eval(q[lane]);
 }
 
 template <int B, bool COUNT>
@@ -702,13 +735,17 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
     int *s_lsrc = s_lbeg + TP::NCL + 1;
     int *s_sc = s_lsrc + TP::NCL;
     const int cap = d.cap;
-    uint2 *s_X = (uint2 *)(smem + TP::bead_off(NT));
-    float2 *s_vel = (float2 *)(s_X + cap);
-    uint32_t *s_id = (uint32_t *)(s_vel + cap);
-    float *s_fx = (float *)(s_id + cap);
-    float *s_fy = s_fx + cap;
-    uint32_t *s_cnt = (uint32_t *)(s_fy + cap);                       // COUNT only
-    uint16_t *s_oslot = (uint16_t *)(COUNT ? (void *)(s_cnt + cap) : (void *)s_cnt);
+    TileArrays t;
+    {
+        unsigned char *p = smem + TP::bead_off(NT);
+        t.X = (uint2 *)p;
+        t.v = (float2 *)(p + 8 * (size_t)cap);
+        t.f = (long long *)(p + 16 * (size_t)cap);
+        t.id = (uint32_t *)(p + 32 * (size_t)cap);
+        t.cnt = (uint32_t *)(p + 36 * (size_t)cap);   // COUNT only
+        t.lc = nullptr;
+    }
+    uint16_t *s_oslot = (uint16_t *)(smem + TP::bead_off(NT) + (COUNT ? 40 : 36) * (size_t)cap);
     unsigned char *s_own = (unsigned char *)(s_oslot + cap);
 
     const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
@@ -761,8 +798,8 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
         int incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += t;
+            const int tt = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += tt;
         }
         int run = incl - sum;
 #pragma unroll
@@ -794,18 +831,18 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
             const bool owned = lx >= 0 && lx < tw && ly >= 0 && ly < th_;
             const uint32_t g = min((uint32_t)(s_lsrc[c] + (s - s_lbeg[c])), n - 1);
             const uint4 xv = d.S_xv[g];
-            s_X[s] = make_uint2(xv.x, xv.y);
-            s_vel[s] = make_float2(vbits(xv.z), vbits(xv.w));
-            s_id[s] = d.S_id[g];
-            s_fx[s] = 0.f;
-            s_fy[s] = 0.f;
-            if (COUNT) s_cnt[s] = 0u;
+            t.X[s] = make_uint2(xv.x, xv.y);
+            t.v[s] = make_float2(vbits(xv.z), vbits(xv.w));
+            t.id[s] = d.S_id[g];
+            t.f[2 * s] = 0;
+            t.f[2 * s + 1] = 0;
+            if (COUNT) t.cnt[s] = 0u;
             s_own[s] = owned ? 1 : 0;
             if (owned) s_oslot[g - g0] = (uint16_t)s;
         }
         __syncthreads();
 
-        pairs_grid<B, COUNT>(d, n_own, x0, y0, tw, s_lbeg, s_X, s_vel, s_id, s_own, s_oslot, s_fx, s_fy, s_cnt,
+        pairs_grid<B, COUNT>(d, n_own, x0, y0, tw, s_lbeg, t, s_own, s_oslot,
                              (uint32_t *)(smem + TP::queue_off(cap, NT, COUNT)) + TP::QLEN * (tid >> 5), s_sc + 1,
                              s_lo, s_hi);
         __syncthreads();
@@ -813,25 +850,25 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
         // ---- integrate owned beads (state read back from shared memory)
         for (int k = tid; k < n_own; k += NT) {
             const int s = s_oslot[k];
-            const uint2 x = s_X[s];
-            const float2 v = s_vel[s];
-            const uint32_t id = s_id[s];
-            if (COUNT && d.pcnt) d.pcnt[id] = s_cnt[s];
-            integrate_bead<B>(d, (int)g0 + k, make_uint4(x.x, x.y, fbits(v.x), fbits(v.y)), id, s_fx[s], s_fy[s],
-                              flags, th);
+            const uint2 x = t.X[s];
+            const float2 v = t.v[s];
+            const uint32_t id = t.id[s];
+            if (COUNT && d.pcnt) d.pcnt[id] = t.cnt[s];
+            integrate_bead<B>(d, (int)g0 + k, make_uint4(x.x, x.y, fbits(v.x), fbits(v.y)), id,
+                              fq_to_f(t.f[2 * s]), fq_to_f(t.f[2 * s + 1]), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
     }
 }
 
-// Fused force + integrate for one tile.  Thread-per-owned-bead pair search:
-// pairs inside the tile are taken once (Newton-3 through shared-memory
-// atomics on the partner's slot), pairs with halo beads are taken from the
-// owned side only (the neighbouring tile takes the other side with the same
-// random number), so every bead's force is complete when the tile finishes
-// and the integration runs in the same kernel.  A tile whose beads do not
-// fit in shared memory takes the same arithmetic from global memory.
+// Fused force + integrate for one tile.  Pairs inside the tile are taken once
+// (Newton-3 through shared-memory atomics on the partner's slot), pairs with
+// halo beads are taken from the owned side only (the neighbouring tile takes
+// the other side and gets exactly the opposite force), so every bead's force
+// is complete when the tile finishes and the integration runs in the same
+// kernel.  A tile whose beads do not fit in shared memory takes the same
+// arithmetic from global memory.
 template <int B, bool COUNT, int VAR>
 __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *smem, Thermo3 &th)
 {
@@ -846,30 +883,15 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     int *s_hg = s_ccnt + TP::NCL;
     int *s_hbeg = s_hg + (TP::NH + 1);
     int *s_hcnt = s_hbeg + (TP::NH + 1);
-    int *s_hsx = s_hcnt + (TP::NH + 1);
-    int *s_hsy = s_hsx + (TP::NH + 1);
-    uint32_t *s_crx = (uint32_t *)(s_hsy + (TP::NH + 1));   // cell corners (fixed point)
-    uint32_t *s_cry = s_crx + (B + 2);
-    int *s_sc = (int *)(s_cry + (B + 2));
+    int *s_sc = s_hcnt + (TP::NH + 1);
     const int cap = d.cap;
-    float2 *s_pos = (float2 *)(smem + TP::bead_off(NT));
-    float2 *s_vel = s_pos + cap;
-    uint32_t *s_id = (uint32_t *)(s_vel + cap);
-    float *s_fx = (float *)(s_id + cap);
-    float *s_fy = s_fx + cap;
-    unsigned char *s_lc = (unsigned char *)(s_fy + cap);
-    uint32_t *s_cnt = (uint32_t *)(smem + ((TP::bead_off(NT) + (size_t)cap * 29 + 3) & ~size_t(3)));  // COUNT only
+    const TileArrays t = tile_arrays<B>(smem, cap, NT, COUNT);
 
     const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
     const int x0 = tx * B, y0 = ty * B;
     const int tw = min(B, d.nc - x0), th_ = min(B, d.nc - y0);
     const int base = y0 * d.nc + x0 * th_;
     const int nh = 2 * (tw + 2) + 2 * th_;
-    // Each staged bead keeps its offset from its own cell's corner
-    // C(c) = ceil(c 2^32 / nc) (exact integer difference, one rounding), so
-    // the precision of a pair separation does not depend on the tile size or
-    // on L; the separation to a bead in the cell (dcx, dcy) away is
-    // off_i - off_j - (dcx, dcy) cs up to one fixed-point unit.
     const uint32_t n = (uint32_t)d.n;
     const long long step = *d.step;
     const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
@@ -879,13 +901,6 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const uint32_t g1 = max(g0, min(d.cstart[base + tw * th_], n));
     const int n_own = (int)(g1 - g0);
 
-    for (int c = tid; c < 2 * (B + 2); c += NT) {
-        const int q = c < B + 2 ? c : c - (B + 2);
-        int cc = (c < B + 2 ? x0 : y0) + q - 1;
-        cc += cc < 0 ? d.nc : (cc >= d.nc ? -d.nc : 0);
-        const uint32_t corner = (uint32_t)((((unsigned long long)cc << 32) + (unsigned)d.nc - 1ull) / (unsigned)d.nc);
-        if (c < B + 2) s_crx[q] = corner; else s_cry[q] = corner;
-    }
     // owned cell table
     for (int c = tid; c < tw * th_; c += NT) {
         const int ly = c / tw, lx = c - ly * tw;
@@ -901,15 +916,13 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         else if (h < 2 * (tw + 2)) { lx = h - (tw + 2) - 1; ly = th_; }
         else if (h < 2 * (tw + 2) + th_) { lx = -1; ly = h - 2 * (tw + 2); }
         else { lx = tw; ly = h - 2 * (tw + 2) - th_; }
-        int cx = x0 + lx, cy = y0 + ly, sx = 0, sy = 0;
-        if (cx < 0) { cx += d.nc; sx = -1; } else if (cx >= d.nc) { cx -= d.nc; sx = 1; }
-        if (cy < 0) { cy += d.nc; sy = -1; } else if (cy >= d.nc) { cy -= d.nc; sy = 1; }
+        int cx = x0 + lx, cy = y0 + ly;
+        cx += cx < 0 ? d.nc : (cx >= d.nc ? -d.nc : 0);
+        cy += cy < 0 ? d.nc : (cy >= d.nc ? -d.nc : 0);
         const int gc = cell_of<B>(d, cx, cy);
         const uint32_t b = min(d.cstart[gc], n), e = min(max(d.cstart[gc + 1], b), n);
         s_hg[h] = (int)b;
         s_hcnt[h] = (int)(e - b);
-        s_hsx[h] = sx;
-        s_hsy[h] = sy;
     }
     __syncthreads();
     if (tid == 0) {
@@ -934,19 +947,19 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const int total = s_sc[0];
 
     if (total <= cap) {
-        // ---- stage owned + halo beads in shared memory (tile-local frame)
+        // ---- stage owned + halo beads in shared memory (raw fixed point:
+        // a periodic image has the same coordinates modulo 2^32)
         for (int k = tid; k < n_own; k += NT) {
             const uint4 xv = d.S_xv[g0 + k];
             const int lx = min(max(cell_coord(d, xv.x) - x0, 0), tw - 1);
             const int ly = min(max(cell_coord(d, xv.y) - y0, 0), th_ - 1);
-            s_pos[k] = make_float2((float)(int)(xv.x - s_crx[lx + 1]) * d.ulen,
-                                   (float)(int)(xv.y - s_cry[ly + 1]) * d.ulen);
-            s_vel[k] = make_float2(vbits(xv.z), vbits(xv.w));
-            s_id[k] = d.S_id[g0 + k];
-            s_fx[k] = 0.f;
-            s_fy[k] = 0.f;
-            if (COUNT) s_cnt[k] = 0u;
-            s_lc[k] = (unsigned char)(lx | (ly << 4));
+            t.X[k] = make_uint2(xv.x, xv.y);
+            t.v[k] = make_float2(vbits(xv.z), vbits(xv.w));
+            t.id[k] = d.S_id[g0 + k];
+            t.f[2 * k] = 0;
+            t.f[2 * k + 1] = 0;
+            if (COUNT) t.cnt[k] = 0u;
+            t.lc[k] = (unsigned char)(lx | (ly << 4));
         }
         for (int k = n_own + tid; k < total; k += NT) {
             int lo = 0, hi = nh - 1;   // last h with hbeg[h] <= k
@@ -955,38 +968,30 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
                 if (s_hbeg[mid] <= k) lo = mid; else hi = mid - 1;
             }
             const int h = lo;
-            const uint32_t gsrc = (uint32_t)s_hg[h] + (uint32_t)(k - s_hbeg[h]);
-            const uint4 xv = d.S_xv[min(gsrc, n - 1)];
-            int hx, hy;   // local cell of halo cell h (perimeter order)
-            if (h < tw + 2) { hx = h - 1; hy = -1; }
-            else if (h < 2 * (tw + 2)) { hx = h - (tw + 2) - 1; hy = th_; }
-            else if (h < 2 * (tw + 2) + th_) { hx = -1; hy = h - 2 * (tw + 2); }
-            else { hx = tw; hy = h - 2 * (tw + 2) - th_; }
-            // the offset from the cell corner is the same for a periodic image
-            s_pos[k] = make_float2((float)(int)(xv.x - s_crx[hx + 1]) * d.ulen,
-                                   (float)(int)(xv.y - s_cry[hy + 1]) * d.ulen);
-            s_vel[k] = make_float2(vbits(xv.z), vbits(xv.w));
-            s_id[k] = d.S_id[min(gsrc, n - 1)];
+            const uint32_t gsrc = min((uint32_t)s_hg[h] + (uint32_t)(k - s_hbeg[h]), n - 1);
+            const uint4 xv = d.S_xv[gsrc];
+            t.X[k] = make_uint2(xv.x, xv.y);
+            t.v[k] = make_float2(vbits(xv.z), vbits(xv.w));
+            t.id[k] = d.S_id[gsrc];
         }
         __syncthreads();
 
         // ---- pair forces
         if (VAR == 1)
-            pairs_thread<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lc,
-                                   s_lo, s_hi);
+            pairs_thread<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, s_lo, s_hi);
         else
-            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, s_pos, s_vel, s_id, s_fx, s_fy, s_cnt, s_lc,
-                                  (uint32_t *)(smem + TP::queue_off(cap, NT, COUNT)) + 128 * (tid >> 5), s_sc + 1, s_lo,
-                                  s_hi);
+            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t,
+                                  (uint32_t *)(smem + TP::queue_off(cap, NT, COUNT)) + 128 * (tid >> 5), s_sc + 1,
+                                  s_lo, s_hi);
         __syncthreads();
 
         // ---- integrate owned beads
         for (int k = tid; k < n_own; k += NT) {
             const int g = (int)g0 + k;
             const uint4 xv = d.S_xv[g];
-            const uint32_t id = s_id[k];
-            if (COUNT && d.pcnt) d.pcnt[id] = s_cnt[k];
-            integrate_bead<B>(d, g, xv, id, s_fx[k], s_fy[k], flags, th);
+            const uint32_t id = t.id[k];
+            if (COUNT && d.pcnt) d.pcnt[id] = t.cnt[k];
+            integrate_bead<B>(d, g, xv, id, fq_to_f(t.f[2 * k]), fq_to_f(t.f[2 * k + 1]), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
@@ -994,7 +999,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
 }
 
 // Block reduction of the thermo partials into the FP64 ring slot of `step`
-// (FP32 inside a warp, FP64 across warps and blocks).
+// (FP64 throughout: per thread, across the warp, across warps and blocks).
 __device__ __forceinline__ void thermo_flush(const Sys &d, Thermo3 th, double *s_red)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -1005,18 +1010,18 @@ __device__ __forceinline__ void thermo_flush(const Sys &d, Thermo3 th, double *s
         th.py += __shfl_xor_sync(0xffffffffu, th.py, o);
     }
     if (lane == 0) {
-        s_red[3 * wid + 0] = (double)th.ke;
-        s_red[3 * wid + 1] = (double)th.px;
-        s_red[3 * wid + 2] = (double)th.py;
+        s_red[3 * wid + 0] = th.ke;
+        s_red[3 * wid + 1] = th.px;
+        s_red[3 * wid + 2] = th.py;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0, c = 0;
         for (int w = 0; w < nw; ++w) { a += s_red[3 * w]; b += s_red[3 * w + 1]; c += s_red[3 * w + 2]; }
-        double *t = d.thermo + 4 * (size_t)(*d.step % THERMO_CAP);
-        atomicAdd(&t[0], a);
-        atomicAdd(&t[1], b);
-        atomicAdd(&t[2], c);
+        double *tt = d.thermo + 4 * (size_t)(*d.step % THERMO_CAP);
+        atomicAdd(&tt[0], a);
+        atomicAdd(&tt[1], b);
+        atomicAdd(&tt[2], c);
     }
 }
 
