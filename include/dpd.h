@@ -83,7 +83,11 @@ typedef struct dpd_params {
                               one of 4, 8, 16                                */
     int32_t variant;       /* pair-kernel variant: 0 = default (fastest),
                               1 = thread-per-bead, 2 = pair queue,
-                              3 = grid-order pair queue                      */
+                              3 = grid-order pair queue, 4 = flat range
+                              enumeration.  tile = variant = 0 takes the
+                              shape dpd_autotune cached for this workload,
+                              else the built-in default.  Every shape gives
+                              the same trajectory bits.                     */
     int32_t reserved;
     double wexp;           /* exponent s of w in the dissipative and random
                               forces (the changed weight exponent the closing
@@ -107,6 +111,17 @@ typedef struct dpd_info {
                                creation (tile + halo above shared capacity)  */
     int64_t device_bytes;   /* device memory held by the context             */
 } dpd_info;
+
+/* Result of a kernel-shape tuning run: every (tile, variant) timed, in ms per
+ * step (-1: the shape did not fit in shared memory), and the fastest. */
+typedef struct dpd_tune_report {
+    int32_t n_shapes;
+    int32_t best_tile, best_variant;
+    int32_t reserved;
+    double best_ms_per_step;
+    int32_t tile[16], variant[16];
+    double ms_per_step[16];
+} dpd_tune_report;
 
 /* Status text (static storage). */
 const char *dpd_status_string(int status);
@@ -183,9 +198,10 @@ int dpd_energy_spectrum(dpd_ctx *ctx, int M, double eps, double *E);
  * pipelined run, where cudaMalloc / cudaFree would synchronise the device).
  * Scratch is one static device array per device of 2,622,464 bytes, so
  * M <= 256 (M > 256 gives DPD_ERR_INVALID_ARG); the per-agent staging of the
- * allocating path is fused into the deposit kernel.  The first call on a
- * device (with that device current) looks up the array's address; make it
- * before any stream capture.  The array is shared by every context on the
+ * allocating path is fused into the deposit kernel.  The device current at
+ * the call must be the one ctx was created on (DPD_ERR_INVALID_ARG
+ * otherwise).  The first call on a device looks up the array's address; make
+ * it before any stream capture.  The array is shared by every context on the
  * device: calls whose stream work overlaps race on it and return wrong
  * values, so serialise them.  Synchronises. */
 int dpd_energy_spectrum_noalloc(dpd_ctx *ctx, int M, double eps, double *E);
@@ -267,6 +283,32 @@ int dpd_batch_barrier_selftest(dpd_batch *b);
 
 /* Replica count, blocks of the persistent launch, (replica, cell block) items. */
 int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
+
+/* Kernel-shape autotuner (no counterpart in the paper: its runs used a CPU
+ * molecular-dynamics code).  The cell-block side B in {4, 8, 16} and the pair
+ * walk variant (1-4) only change how the step's work is cut into CTAs and
+ * lanes; all shapes give bit-identical trajectories.
+ *
+ * dpd_autotune creates a temporary context per shape on `stream` (device
+ * memory of one context at a time), loads x, v (id order, [N][2]; `where`
+ * says host or device; x = NULL: dpd_init_random(p->seed)), runs two warm-up
+ * steps, times `steps` steps twice with CUDA events on the context's stream
+ * and keeps the better time.  The fastest shape is returned in rep and cached
+ * (process-wide, thread-safe) under the key (n_beads, L, r_c); dpd_create
+ * with tile = variant = 0 then uses it.  dpd_batch_autotune does the same for
+ * a batch of R replicas (variants 2-4; key: R, sum of N, sum of L^2, sum of
+ * N^2) from dpd_batch_init_random(p[0].seed); dpd_batch_create with
+ * p[0].tile = p[0].variant = 0 uses it.  Errors of a run are returned as is;
+ * DPD_ERR_INVALID_ARG if no shape fits.  dpd_tune_store seeds the cache with a
+ * known shape (R = 1: single system), dpd_tune_lookup reads it
+ * (DPD_ERR_STATE: not cached), dpd_tune_clear empties it; these three are
+ * host-only. */
+int dpd_autotune(const dpd_params *p, const double *x, const float *v, int where, int steps, void *stream,
+                 dpd_tune_report *rep);
+int dpd_batch_autotune(const dpd_params *p, int R, int steps, void *stream, dpd_tune_report *rep);
+int dpd_tune_store(const dpd_params *p, int R, int tile, int variant);
+int dpd_tune_lookup(const dpd_params *p, int R, int *tile, int *variant);
+void dpd_tune_clear(void);
 
 /* ------------------------------------------------------------------------
  * Three-dimensional variant.  Sec. 2 states every force as a vector law; the

@@ -16,6 +16,6 @@ def __getattr__(name):
         return importlib.import_module(__name__ + ".surrogate").Surrogate
     if name == "Ensemble":
         return importlib.import_module(__name__ + ".ensemble").Ensemble
-    if name in ("synth", "sim", "build", "ensemble", "surrogate", "study"):
+    if name in ("synth", "sim", "build", "ensemble", "surrogate", "study", "tune"):
         return importlib.import_module(__name__ + "." + name)
     raise AttributeError(name)

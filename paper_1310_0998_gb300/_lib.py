@@ -65,6 +65,26 @@ class DpdInfo(ctypes.Structure):
     ]
 
 
+class DpdTuneReport(ctypes.Structure):
+    _fields_ = [
+        ("n_shapes", ctypes.c_int32),
+        ("best_tile", ctypes.c_int32),
+        ("best_variant", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("best_ms_per_step", ctypes.c_double),
+        ("tile", ctypes.c_int32 * 16),
+        ("variant", ctypes.c_int32 * 16),
+        ("ms_per_step", ctypes.c_double * 16),
+    ]
+
+    def as_dict(self):
+        n = self.n_shapes
+        return {"best": {"tile": self.best_tile, "variant": self.best_variant,
+                         "ms_per_step": self.best_ms_per_step},
+                "shapes": [{"tile": self.tile[i], "variant": self.variant[i],
+                            "ms_per_step": self.ms_per_step[i]} for i in range(n)]}
+
+
 class SurProtocol(ctypes.Structure):
     _fields_ = [
         ("L", ctypes.c_double),
@@ -115,6 +135,11 @@ def _declare(L):
         "dpd_batch_sync": ([vp], c_int),
         "dpd_batch_barrier_selftest": ([vp], c_int),
         "dpd_batch_info": ([vp, P(c_int), P(c_int), P(c_int)], c_int),
+        "dpd_autotune": ([P(DpdParams), vp, vp, c_int, c_int, vp, P(DpdTuneReport)], c_int),
+        "dpd_batch_autotune": ([vp, c_int, c_int, vp, P(DpdTuneReport)], c_int),
+        "dpd_tune_store": ([P(DpdParams), c_int, c_int, c_int], c_int),
+        "dpd_tune_lookup": ([P(DpdParams), c_int, P(c_int), P(c_int)], c_int),
+        "dpd_tune_clear": ([], None),
         "dpd3_create": ([P(DpdParams), vp, P(vp)], c_int),
         "dpd3_destroy": ([vp], None),
         "dpd3_set_state": ([vp, vp, vp, i64], c_int),

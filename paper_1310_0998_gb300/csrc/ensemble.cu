@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
             Thermo3 th{0.0, 0.0, 0.0};
             force_tile<B, false, VAR>(d, (int)(w & 0x3fffffu), flags, smem, th);
             __syncthreads();
-            thermo_flush(d, th, (double *)(smem + TilePlan<B>::red_off()));
+            thermo_flush(d, th, (double *)(smem + tile_red_off<B, VAR>()));
             __syncthreads();
         }
         grid_barrier(bar, nb, berr, 0);
@@ -169,6 +169,7 @@ static int ens_dispatch_prepare(dpd_batch *b)
 {
     if (b->var == 1) return b->B == 4 ? ens_prepare<4, 1>(b) : b->B == 8 ? ens_prepare<8, 1>(b) : ens_prepare<16, 1>(b);
     if (b->var == 3) return b->B == 4 ? ens_prepare<4, 3>(b) : b->B == 8 ? ens_prepare<8, 3>(b) : ens_prepare<16, 3>(b);
+    if (b->var == 4) return b->B == 4 ? ens_prepare<4, 4>(b) : b->B == 8 ? ens_prepare<8, 4>(b) : ens_prepare<16, 4>(b);
     return b->B == 4 ? ens_prepare<4, 2>(b) : b->B == 8 ? ens_prepare<8, 2>(b) : ens_prepare<16, 2>(b);
 }
 
@@ -182,6 +183,10 @@ static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last)
         if (b->B == 4) ens_launch<4, 3>(b, nsteps, final_last);
         else if (b->B == 8) ens_launch<8, 3>(b, nsteps, final_last);
         else ens_launch<16, 3>(b, nsteps, final_last);
+    } else if (b->var == 4) {
+        if (b->B == 4) ens_launch<4, 4>(b, nsteps, final_last);
+        else if (b->B == 8) ens_launch<8, 4>(b, nsteps, final_last);
+        else ens_launch<16, 4>(b, nsteps, final_last);
     } else {
         if (b->B == 4) ens_launch<4, 2>(b, nsteps, final_last);
         else if (b->B == 8) ens_launch<8, 2>(b, nsteps, final_last);
@@ -260,8 +265,15 @@ int dpd_batch_create(const dpd_params *p, int R, void *stream, dpd_batch **out)
     for (int r = 0; r < R; ++r) {
         const int rc = validate(&p[r]);
         if (rc) return rc;
-        if ((p[r].tile ? p[r].tile : 8) != (p[0].tile ? p[0].tile : 8) || p[r].variant != p[0].variant)
+        if (p[r].tile != p[0].tile || p[r].variant != p[0].variant)
             return DPD_ERR_INVALID_ARG;   // one kernel shape for the whole batch
+    }
+    // one shape for every replica: the caller's, the tuned one, or the default
+    std::vector<dpd_params> q(p, p + R);
+    {
+        int t = p[0].tile ? p[0].tile : DEFAULT_TILE, v = p[0].variant ? p[0].variant : DEFAULT_VARIANT;
+        if (!p[0].tile && !p[0].variant) tuned_shape(p, R, &t, &v);
+        for (auto &e : q) { e.tile = t; e.variant = v; }
     }
     dpd_batch *b = new (std::nothrow) dpd_batch();
     if (!b) return DPD_ERR_OOM;
@@ -272,12 +284,12 @@ int dpd_batch_create(const dpd_params *p, int R, void *stream, dpd_batch **out)
         if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) { delete b; return DPD_ERR_CUDA; }
         b->own_stream = true;
     }
-    b->B = p[0].tile ? p[0].tile : 8;
-    b->var = p[0].variant ? p[0].variant : 2;
+    b->B = q[0].tile;
+    b->var = q[0].variant;
     b->reps.assign(R, nullptr);
     int rc = DPD_OK;
     for (int r = 0; r < R && rc == DPD_OK; ++r) {
-        rc = dpd_create(&p[r], b->st, &b->reps[r]);
+        rc = dpd_create(&q[r], b->st, &b->reps[r]);
         if (rc == DPD_OK) b->reps[r]->batch_owned = true;
     }
     if (rc == DPD_OK && cudaMallocHost((void **)&b->h_pin, 64) != cudaSuccess) rc = DPD_ERR_OOM;

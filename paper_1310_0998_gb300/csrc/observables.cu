@@ -479,12 +479,14 @@ static __device__ __align__(256) double g_spectrum_scratch[NOALLOC_DOUBLES];
 static double *g_spectrum_scratch_ptr[NOALLOC_MAX_DEVICES];
 static std::mutex g_spectrum_scratch_mu;
 
-// Device address of the static scratch for the current device (set-up on the
-// first call per device).
-static int spectrum_scratch(double **out)
+// Device address of the static scratch on the context's device (set-up on the
+// first call per device).  The symbol lookup answers for the current device,
+// so that must be the device the context was created on.
+static int spectrum_scratch(int ctx_dev, double **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return DPD_ERR_CUDA;
+    if (dev != ctx_dev) return DPD_ERR_INVALID_ARG;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DPD_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_spectrum_scratch_mu);
     if (!g_spectrum_scratch_ptr[dev]) {
@@ -541,7 +543,7 @@ extern "C" int dpd_energy_spectrum_noalloc(dpd_ctx *c, int M, double eps, double
     if (eps <= 0.0) eps = L * std::sqrt(10.0 / (double)na);
     if (eps / (L / M) > 56.0) return DPD_ERR_INVALID_ARG;
     double *scr = nullptr;
-    const int rc = spectrum_scratch(&scr);
+    const int rc = spectrum_scratch(c->dev, &scr);
     if (rc) return rc;
     const size_t MM = (size_t)M * M;
     double *sx = scr, *sy = sx + MM, *cn = sy + MM;

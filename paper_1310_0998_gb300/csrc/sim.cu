@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 10) k_force(Sys d, int flags)
     force_tile<B, COUNT, VAR>(d, blockIdx.x, flags, smem, th);
     if (flags & (F_ADVANCE | F_FINAL)) {
         __syncthreads();
-        thermo_flush(d, th, (double *)(smem + TilePlan<B>::red_off()));
+        thermo_flush(d, th, (double *)(smem + tile_red_off<B, VAR>()));
     }
 }
 
@@ -196,7 +196,7 @@ int validate(const dpd_params *p)
         return DPD_ERR_INVALID_ARG;
     if (p->n_beads < 2 || (p->n_beads & 1) || p->n_beads >= (1ll << 31)) return DPD_ERR_INVALID_ARG;
     if (!(p->tile == 0 || p->tile == 4 || p->tile == 8 || p->tile == 16)) return DPD_ERR_INVALID_ARG;
-    if (p->variant < 0 || p->variant > 3) return DPD_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 4) return DPD_ERR_INVALID_ARG;
     if (p->noise < 0 || p->noise > 1) return DPD_ERR_INVALID_ARG;
     if (!(p->wexp >= 0.0 && p->wexp <= 8.0)) return DPD_ERR_INVALID_ARG;
     const int nc = n_cells_side(p->L, p->rc);
@@ -275,6 +275,13 @@ size_t force_smem(int B, int var, int cap, bool count)
             default: return TilePlanG<16>::bytes(cap, TILE_THREADS, count);
         }
     }
+    if (var == 4) {
+        switch (B) {
+            case 4: return TilePlan<4, 4>::bytes(cap, TILE_THREADS, count);
+            case 8: return TilePlan<8, 4>::bytes(cap, TILE_THREADS, count);
+            default: return TilePlan<16, 4>::bytes(cap, TILE_THREADS, count);
+        }
+    }
     switch (B) {
         case 4: return TilePlan<4>::bytes(cap, TILE_THREADS, count);
         case 8: return TilePlan<8>::bytes(cap, TILE_THREADS, count);
@@ -303,6 +310,8 @@ static int set_force_attrs(int smax)
     if (!rc) rc = set_dyn_limit(k_force<B, true, 2>, smax);
     if (!rc) rc = set_dyn_limit(k_force<B, false, 3>, smax);
     if (!rc) rc = set_dyn_limit(k_force<B, true, 3>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, false, 4>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, true, 4>, smax);
     return rc;
 }
 
@@ -345,6 +354,12 @@ void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t sme
             case 4: launch_force_t<4, 3>(d, st, smem, flags, count); break;
             case 8: launch_force_t<8, 3>(d, st, smem, flags, count); break;
             default: launch_force_t<16, 3>(d, st, smem, flags, count); break;
+        }
+    } else if (var == 4) {
+        switch (B) {
+            case 4: launch_force_t<4, 4>(d, st, smem, flags, count); break;
+            case 8: launch_force_t<8, 4>(d, st, smem, flags, count); break;
+            default: launch_force_t<16, 4>(d, st, smem, flags, count); break;
         }
     } else {
         switch (B) {
@@ -497,9 +512,14 @@ int dpd_create(const dpd_params *p, void *stream, dpd_ctx **out)
     if (rc) return rc;
     dpd_ctx *c = new (std::nothrow) dpd_ctx();
     if (!c) return DPD_ERR_OOM;
+    if (cudaGetDevice(&c->dev) != cudaSuccess) { delete c; return DPD_ERR_CUDA; }
     c->p = *p;
-    c->B = p->tile ? p->tile : 8;
-    c->var = p->variant ? p->variant : 2;
+    c->B = p->tile ? p->tile : DEFAULT_TILE;
+    c->var = p->variant ? p->variant : DEFAULT_VARIANT;
+    if (!p->tile && !p->variant) {
+        int t = 0, v = 0;
+        if (tuned_shape(p, 1, &t, &v)) { c->B = t; c->var = v; }
+    }
     if (stream) {
         c->st = (cudaStream_t)stream;
     } else {
@@ -586,9 +606,9 @@ int dpd_set_params(dpd_ctx *c, const dpd_params *p)
     int rc = validate(p);
     if (rc) return rc;
     if (p->n_beads != c->p.n_beads || p->L != c->p.L || p->rc != c->p.rc) return DPD_ERR_STATE;
-    const int B = p->tile ? p->tile : 8;
+    const int B = p->tile ? p->tile : c->B;
     if (B != c->B) return DPD_ERR_STATE;
-    c->var = p->variant ? p->variant : 2;
+    c->var = p->variant ? p->variant : c->var;
     c->p = *p;
     fill_physics(c->d, p);
     free_graphs(c);   // kernel arguments carry the parameters

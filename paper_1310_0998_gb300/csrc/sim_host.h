@@ -20,6 +20,8 @@ int max_dynamic_smem();
 void launch_bin(const Sys &d, int B, cudaStream_t st);
 void launch_kick_bin(const Sys &d, int B, cudaStream_t st);
 int host_cell_of(int B, int nc, int cx, int cy);
+bool tuned_shape(const dpd_params *p, int R, int *tile, int *variant);
+constexpr int DEFAULT_TILE = 8, DEFAULT_VARIANT = 2;
 }  // namespace dpd
 
 struct dpd_ctx {
@@ -41,6 +43,7 @@ struct dpd_ctx {
     void *obs = nullptr;            // observables scratch (observables.cu)
     void *stage = nullptr;          // 32 B/bead staging for host state transfers
     unsigned long long ovf_seen = 0;  // overflowed tiles already answered by a larger capacity
+    int dev = -1;                   // CUDA device current at creation (owns every buffer)
 };
 
 int dpd_internal_latched(dpd_ctx *c);

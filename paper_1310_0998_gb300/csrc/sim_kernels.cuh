@@ -217,6 +217,10 @@ template <int B>
 __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, uint32_t id, float fx, float fy,
                                                int flags, Thermo3 &th)
 {
+    if (id >= (uint32_t)d.n) {
+        set_err_at(d, ERR_INTERNAL, 7, g, id, d.n);
+        return;
+    }
     const uint32_t ps = d.slot[id ^ 1u];
     if (ps < (uint32_t)d.n) {
         const uint4 xp = d.S_xv[ps];
@@ -315,13 +319,20 @@ __device__ __forceinline__ void pair_force_q(const Sys &d, uint2 xi, uint2 xj, f
 }
 
 // ------------------------------------------------------------ force tile ----
-// Shared-memory plan of one tile (B x B owned cells + one-cell halo).
+// Shared-memory plan of one tile (B x B owned cells + one-cell halo) for the
+// variants that stage owned beads first (1, 2, 4).  Variant 4 adds, per owned
+// cell, its merged candidate ranges (FLAT_MAXI at most) and a per-warp table
+// of the 32 ranges being enumerated.
 constexpr int TILE_THREADS = 128;
-template <int B>
+constexpr int FLAT_MAXI = 6;
+template <int B, int VAR = 2>
 struct TilePlan {
     static constexpr int NCL = (B + 2) * (B + 2);   // local cell table
     static constexpr int NH = 4 * B + 4;            // halo cells
-    static constexpr int NINT = 2 * NCL + 3 * (NH + 1) + 8;
+    static constexpr int NITEM = VAR == 4 ? B * B * (FLAT_MAXI + 1) : 0;
+    static constexpr int NINT = 2 * NCL + 3 * (NH + 1) + 8 + NITEM;
+    static constexpr int QLEN = VAR == 4 ? 64 : 128;            // queue entries per warp
+    static constexpr int WARP_BYTES = 4 * QLEN + (VAR == 4 ? 16 * 32 : 0);
     static __host__ __device__ size_t red_off() { return ((size_t)NINT * 4 + 7) & ~size_t(7); }
     static __host__ __device__ size_t bead_off(int nthreads)
     {
@@ -336,7 +347,7 @@ struct TilePlan {
     }
     static __host__ __device__ size_t bytes(int cap, int nthreads, bool count)
     {
-        return queue_off(cap, nthreads, count) + sizeof(uint32_t) * 128 * (size_t)(nthreads / 32);
+        return queue_off(cap, nthreads, count) + (size_t)WARP_BYTES * (size_t)(nthreads / 32);
     }
 };
 
@@ -351,11 +362,11 @@ struct TileArrays {
     unsigned char *lc; // local cell (lx | ly << 4) of an owned bead
 };
 
-template <int B>
+template <int B, int VAR>
 __device__ __forceinline__ TileArrays tile_arrays(unsigned char *smem, int cap, int nthreads, bool count)
 {
     TileArrays a;
-    unsigned char *p = smem + TilePlan<B>::bead_off(nthreads);
+    unsigned char *p = smem + TilePlan<B, VAR>::bead_off(nthreads);
     a.X = (uint2 *)p;
     a.v = (float2 *)(p + 8 * (size_t)cap);
     a.f = (long long *)(p + 16 * (size_t)cap);
@@ -537,6 +548,163 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
         qn += n0 + __popc(m1);
         __syncwarp();
         queue_drain<2>(q, qn, eval);
+    }
+    __syncwarp();
+    if (lane < qn) eval(q[lane]);
+}
+
+// Variant 4: flat enumeration.  Every owned cell has a short list of candidate
+// ranges of the staged beads, built once per tile: its own cell (a bead starts
+// after itself) merged with whatever owned cells follow contiguously (E), the
+// row ahead (NW, N, NE, contiguous when owned or all in the top halo row) and
+// the halo cells behind, adjacent ranges merged.  Each lane holds one range of
+// one bead at a time; the warp concatenates its 32 current ranges (exclusive
+// scan of their lengths) and tests the concatenation 32 candidates at a time,
+// lane l taking candidate t0 + l, so every lane tests a candidate in every
+// round whatever the range lengths.  A lane finds the range that holds its
+// candidate from the bit mask of range starts inside the round (an OR across
+// the warp) and a popcount.  Pairs inside r_c go through the warp's pair
+// queue as in variant 2.  Every shared-memory index the walk derives is
+// checked against the tile (a failed check is reported and the candidate
+// dropped).
+template <int B>
+__device__ __forceinline__ void flat_cell_items(const Sys &d, int tw, int th_, int n_own, const int *s_cbeg,
+                                                const int *s_ccnt, int *s_nit, uint32_t *s_items)
+{
+    for (int oc = threadIdx.x; oc < tw * th_; oc += blockDim.x) {
+        const int ly = oc / tw, lx = oc - ly * tw;
+        // keys (begin << 14) | (end << 1) | newton of the visited neighbour
+        // cells; the own cell stays first (it has the lowest begin of the
+        // owned cells, and halo beads are staged after all owned ones)
+        uint32_t own = 0, key[8];
+#pragma unroll
+        for (int nb = 0; nb < 9; ++nb) {
+            const int ox_ = (int)((NB_DX >> (2 * nb)) & 3u) - 1, oy_ = (int)((NB_DY >> (2 * nb)) & 3u) - 1;
+            const int nlx = lx + ox_, nly = ly + oy_;
+            const bool owned = (nlx >= 0 && nlx < tw && nly >= 0 && nly < th_);
+            const int lc = (nly + 1) * (B + 2) + nlx + 1;
+            const uint32_t b = (uint32_t)s_cbeg[lc], e = b + (uint32_t)s_ccnt[lc];
+            const uint32_t k = (b << 14) | (e << 1) | (owned ? 1u : 0u);
+            if (nb == 0) own = k;
+            else key[nb - 1] = (nb >= 5 && owned) ? 0xffffffffu : k;   // behind: only halo cells
+        }
+        // sort the eight neighbour keys by begin (Batcher's network)
+#define DPD_CE(a, b)                                                   \
+        { const uint32_t lo_ = min(key[a], key[b]), hi_ = max(key[a], key[b]); key[a] = lo_; key[b] = hi_; }
+        DPD_CE(0, 1) DPD_CE(2, 3) DPD_CE(4, 5) DPD_CE(6, 7)
+        DPD_CE(0, 2) DPD_CE(1, 3) DPD_CE(4, 6) DPD_CE(5, 7)
+        DPD_CE(1, 2) DPD_CE(5, 6)
+        DPD_CE(0, 4) DPD_CE(1, 5) DPD_CE(2, 6) DPD_CE(3, 7)
+        DPD_CE(2, 4) DPD_CE(3, 5)
+        DPD_CE(1, 2) DPD_CE(3, 4) DPD_CE(5, 6)
+#undef DPD_CE
+        // merge ranges that continue each other with the same Newton-3 side
+        uint32_t cb = own >> 14, ce = (own >> 1) & 0x1fffu, cn = own & 1u;
+        int m = 0;
+        bool first = true;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t k = key[i];
+            if (k == 0xffffffffu) continue;
+            const uint32_t b = k >> 14, e = (k >> 1) & 0x1fffu, nw = k & 1u;
+            if (b == ce && nw == cn) { ce = e; continue; }
+            if (e == b) continue;
+            if (first || ce > cb) {
+                if (m < FLAT_MAXI) s_items[oc * FLAT_MAXI + m] = cb | (ce << 13) | (cn << 26);
+                ++m;
+            }
+            first = false;
+            cb = b; ce = e; cn = nw;
+        }
+        if (first || ce > cb) {
+            if (m < FLAT_MAXI) s_items[oc * FLAT_MAXI + m] = cb | (ce << 13) | (cn << 26);
+            ++m;
+        }
+        if (m > FLAT_MAXI) set_err_at(d, ERR_INTERNAL, 5, oc, m, n_own);
+        s_nit[oc] = min(m, FLAT_MAXI);
+    }
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void pairs_flat(const Sys &d, int n_own, int total, int tw, const TileArrays &t,
+                                           const int *s_nit, const uint32_t *s_items, uint4 *rec,
+                                           volatile uint32_t *q, int *s_next, uint32_t s_lo, uint32_t s_hi)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u, le = (2u << lane) - 1u;
+    int k = 0, ii = 0, ni = 0, oc = 0;
+    uint32_t b = 0, e = 0, nw = 0, pid = 0;
+    uint2 xi = make_uint2(0u, 0u);
+    bool more = true;
+    int qn = 0;   // warp-uniform queue length
+    auto eval = [&](uint32_t code) { queue_eval<COUNT>(d, code, t, s_lo, s_hi); };
+    while (true) {
+        // this lane's next non-empty range (at most FLAT_MAXI + 1 per bead)
+        while (more && b >= e) {
+            if (ii >= ni) {
+                k = atomicAdd(s_next, 1);
+                if (k >= n_own) { more = false; break; }
+                const uint32_t lc = t.lc[k];
+                oc = (int)(lc >> 4) * tw + (int)(lc & 15u);
+                ni = s_nit[oc];
+                ii = 0;
+                xi = t.X[k];
+                pid = d.excl ? (t.id[k] ^ 1u) : 0xffffffffu;
+            }
+            const uint32_t it = s_items[oc * FLAT_MAXI + min(ii, FLAT_MAXI - 1)];
+            b = ii == 0 ? (uint32_t)k + 1u : (it & 0x1fffu);
+            e = (it >> 13) & 0x1fffu;
+            nw = (it >> 26) & 1u;
+            ++ii;
+        }
+        const uint32_t len = b < e ? e - b : 0u;
+        const unsigned ne = __ballot_sync(FULL, len > 0u);
+        if (ne == 0u) break;
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t start = incl - len, T = __shfl_sync(FULL, incl, 31);
+        // ranges in rank order: bead position, exclusion id, and
+        // (bead slot | Newton-3 flag << 12 | (range begin - start) << 13)
+        if (len > 0u)
+            rec[__popc(ne & lt)] = make_uint4(xi.x, xi.y, pid, (uint32_t)k | (nw << 12) | ((b - start) << 13));
+        __syncwarp();
+        int c0 = 0;   // ranges that start before this round
+        for (uint32_t t0 = 0; t0 < T; t0 += 32u) {
+            const bool inb = (len > 0u) & (start >= t0) & (start < t0 + 32u);
+            // OR of the start bits across the warp (a shuffle butterfly: the
+            // warp OR-reduction instruction gave wrong masks in this loop)
+            unsigned M = inb ? (1u << (start - t0)) : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) M |= __shfl_xor_sync(FULL, M, o);
+            const int r = c0 + __popc(M & le) - 1;
+            c0 += __popc(M);
+            const uint32_t f = t0 + (uint32_t)lane;
+            bool p = false;
+            uint32_t code = 0;
+            if (f < T) {
+                const uint4 rc = rec[r & 31];
+                const uint32_t j = f + (uint32_t)((int)rc.w >> 13);
+                if (r >= 0 && r < 32 && j < (uint32_t)total && (rc.w & 0xfffu) < (uint32_t)n_own) {
+                    const uint2 xj = t.X[j];
+                    p = in_range(d, r2_u(sep_u(rc.x, xj.x), sep_u(rc.y, xj.y))) & (t.id[j] != rc.z);
+                    code = (rc.w & 0xfffu) | (j << 12) | (((rc.w >> 12) & 1u) << 24);
+                } else {
+                    set_err_at(d, ERR_INTERNAL, 6, r, (long long)j, total);
+                }
+            }
+            const unsigned m = __ballot_sync(FULL, p);
+            if (p) q[qn + __popc(m & lt)] = code;
+            qn += __popc(m);
+            __syncwarp();
+            queue_drain<1>(q, qn, eval);
+        }
+        b = e;
+        __syncwarp();
     }
     __syncwarp();
     if (lane < qn) eval(q[lane]);
@@ -876,7 +1044,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         force_tile_g<B, COUNT>(d, tile, flags, smem, th);
         return;
     }
-    using TP = TilePlan<B>;
+    using TP = TilePlan<B, VAR>;
     const int NT = blockDim.x, tid = threadIdx.x;
     int *s_cbeg = (int *)smem;
     int *s_ccnt = s_cbeg + TP::NCL;
@@ -884,8 +1052,10 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     int *s_hbeg = s_hg + (TP::NH + 1);
     int *s_hcnt = s_hbeg + (TP::NH + 1);
     int *s_sc = s_hcnt + (TP::NH + 1);
+    int *s_nit = s_sc + 8;                            // variant 4: ranges per owned cell
+    uint32_t *s_items = (uint32_t *)(s_nit + B * B);  // variant 4: the ranges
     const int cap = d.cap;
-    const TileArrays t = tile_arrays<B>(smem, cap, NT, COUNT);
+    const TileArrays t = tile_arrays<B, VAR>(smem, cap, NT, COUNT);
 
     const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
     const int x0 = tx * B, y0 = ty * B;
@@ -977,12 +1147,17 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         __syncthreads();
 
         // ---- pair forces
-        if (VAR == 1)
+        unsigned char *wbuf = smem + TP::queue_off(cap, NT, COUNT) + (size_t)TP::WARP_BYTES * (tid >> 5);
+        if constexpr (VAR == 1) {
             pairs_thread<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, s_lo, s_hi);
-        else
-            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t,
-                                  (uint32_t *)(smem + TP::queue_off(cap, NT, COUNT)) + 128 * (tid >> 5), s_sc + 1,
-                                  s_lo, s_hi);
+        } else if constexpr (VAR == 4) {
+            flat_cell_items<B>(d, tw, th_, n_own, s_cbeg, s_ccnt, s_nit, s_items);
+            __syncthreads();
+            pairs_flat<COUNT>(d, n_own, total, tw, t, s_nit, s_items, (uint4 *)wbuf, (uint32_t *)(wbuf + 16 * 32),
+                              s_sc + 1, s_lo, s_hi);
+        } else {
+            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi);
+        }
         __syncthreads();
 
         // ---- integrate owned beads
@@ -990,12 +1165,20 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             const int g = (int)g0 + k;
             const uint4 xv = d.S_xv[g];
             const uint32_t id = t.id[k];
-            if (COUNT && d.pcnt) d.pcnt[id] = t.cnt[k];
+            if (COUNT && d.pcnt && id < (uint32_t)d.n) d.pcnt[id] = t.cnt[k];
             integrate_bead<B>(d, g, xv, id, fq_to_f(t.f[2 * k]), fq_to_f(t.f[2 * k + 1]), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
     }
+}
+
+// Shared-memory offset of the thermo reduction buffer of a variant's tile plan.
+template <int B, int VAR>
+__host__ __device__ inline size_t tile_red_off()
+{
+    if constexpr (VAR == 3) return TilePlanG<B>::red_off();
+    else return TilePlan<B, VAR>::red_off();
 }
 
 // Block reduction of the thermo partials into the FP64 ring slot of `step`
