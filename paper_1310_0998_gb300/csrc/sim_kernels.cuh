@@ -190,20 +190,30 @@ __device__ __forceinline__ void bin_one(const Sys &d, int k)
 // Thermo partials of one thread, FP64: sum |v|^2, sum v_x, sum v_y.
 struct Thermo3 { double ke, px, py; };
 
-// Pair forces are summed per bead as 64-bit fixed point, 2^-32 force units per
-// count.  Integer addition is associative, so a bead's force does not depend on
-// the order in which its pairs are met (the in-cell order of the counting sort
-// comes from atomic tickets and varies from run to run); every FP32 pair
-// contribution of magnitude 2^-9 or more converts exactly.  A pair force of
+// Pair forces are summed per bead in fixed point, 2^-24 force units per
+// count.  Integer addition is associative, so a bead's force does not depend
+// on the order in which its pairs are met (the in-cell order of the counting
+// sort comes from atomic tickets and varies from run to run); every FP32 pair
+// contribution of magnitude 1/2 or more converts exactly.  In shared memory a
+// component is two 32-bit words updated with native integer atomics: hi, the
+// count shifted right by 16 (signed), and lo, its low 16 bits (unsigned); the
+// sum is hi 2^16 + lo exactly as long as a bead meets fewer than 2^16 pairs and
+// its pair forces add up to less than 2^23 in magnitude.  A pair force of
 // magnitude FQ_MAX or more (a blown-up state) is reported as non-finite.
-constexpr float FQ_SCALE = 4294967296.0f;            // 2^32
-constexpr float FQ_INV = 2.3283064365386963e-10f;    // 2^-32
-constexpr float FQ_MAX = 1.0e8f;
+constexpr float FQ_SCALE = 16777216.0f;              // 2^24
+constexpr float FQ_INV = 5.9604644775390625e-08f;    // 2^-24
+constexpr float FQ_MAX = 65536.0f;
 __device__ __forceinline__ long long fq(float g) { return __float2ll_rn(__fmul_rn(g, FQ_SCALE)); }
 __device__ __forceinline__ float fq_to_f(long long q) { return __fmul_rn(__ll2float_rn(q), FQ_INV); }
-__device__ __forceinline__ void fq_add(long long *a, long long q)
+// a: the (hi, lo) words of one force component in shared memory
+__device__ __forceinline__ void fq_add(int *a, long long q)
 {
-    atomicAdd((unsigned long long *)a, (unsigned long long)q);
+    atomicAdd(a, (int)(q >> 16));
+    atomicAdd((unsigned *)(a + 1), (unsigned)(q & 0xffffll));
+}
+__device__ __forceinline__ float fq_load(const int *a)
+{
+    return fq_to_f((long long)a[0] * 65536ll + (long long)(unsigned)a[1]);
 }
 
 // Everything after the pair sum for one owned bead at sorted slot g:
@@ -280,7 +290,14 @@ __device__ __forceinline__ void integrate_bead(const Sys &d, int g, uint4 xv, ui
 // both sides.
 __device__ __forceinline__ float sep_u(uint32_t a, uint32_t b) { return (float)(int)(a - b); }
 __device__ __forceinline__ float r2_u(float ux, float uy) { return __fmaf_rn(ux, ux, __fmul_rn(uy, uy)); }
-__device__ __forceinline__ bool in_range(const Sys &d, float r2u) { return (r2u < d.rc2u) & (r2u > 0.f); }
+// The pair test r < r_c on the FP32 square of the separation in units (every
+// kernel and path takes this same decision from the same two positions, so
+// the set of interacting pairs is a property of the positions alone).
+__device__ __forceinline__ bool in_range(const Sys &d, uint32_t xa, uint32_t ya, uint32_t xb, uint32_t yb)
+{
+    const float r2u = r2_u(sep_u(xa, xb), sep_u(ya, yb));
+    return (r2u < d.rc2u) & (r2u > 0.f);
+}
 
 // Scalar F of the pair force F e_ij (Eqs. DPDf, DPDcdr, weightFunc01):
 // F = w [a - gamma w (v_ij . e_ij) + sigma alpha_ij / sqrt(dt)], w = 1 - r / r_c,
@@ -356,7 +373,7 @@ struct TilePlan {
 struct TileArrays {
     uint2 *X;          // fixed-point position
     float2 *v;         // velocity
-    long long *f;      // force counts (x, y) of the pairs met so far
+    int *f;            // force counts: (hi, lo) words of x, then of y
     uint32_t *id;
     uint32_t *cnt;     // interacting neighbours (COUNT only)
     unsigned char *lc; // local cell (lx | ly << 4) of an owned bead
@@ -369,7 +386,7 @@ __device__ __forceinline__ TileArrays tile_arrays(unsigned char *smem, int cap, 
     unsigned char *p = smem + TilePlan<B, VAR>::bead_off(nthreads);
     a.X = (uint2 *)p;
     a.v = (float2 *)(p + 8 * (size_t)cap);
-    a.f = (long long *)(p + 16 * (size_t)cap);
+    a.f = (int *)(p + 16 * (size_t)cap);
     a.id = (uint32_t *)(p + 32 * (size_t)cap);
     a.cnt = (uint32_t *)(p + 36 * (size_t)cap);
     a.lc = p + (count ? 40 : 36) * (size_t)cap;
@@ -409,7 +426,7 @@ __device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, in
             if (nb == 0) j = k + 1;
             for (; j < je; ++j) {
                 const uint2 xj = t.X[j];
-                if (!in_range(d, r2_u(sep_u(xi.x, xj.x), sep_u(xi.y, xj.y)))) continue;
+                if (!in_range(d, xi.x, xi.y, xj.x, xj.y)) continue;
                 const uint32_t idj = t.id[j];
                 if (idj == pid) continue;
                 long long qx, qy;
@@ -418,14 +435,14 @@ __device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, in
                 fy += qy;
                 if (COUNT) ++cnt;
                 if (owned) {
-                    fq_add(&t.f[2 * j], -qx);
-                    fq_add(&t.f[2 * j + 1], -qy);
+                    fq_add(&t.f[4 * j], -qx);
+                    fq_add(&t.f[4 * j + 2], -qy);
                     if (COUNT) atomicAdd(&t.cnt[j], 1u);
                 }
             }
         }
-        fq_add(&t.f[2 * k], fx);
-        fq_add(&t.f[2 * k + 1], fy);
+        fq_add(&t.f[4 * k], fx);
+        fq_add(&t.f[4 * k + 2], fy);
         if (COUNT) atomicAdd(&t.cnt[k], cnt);
     }
 }
@@ -444,12 +461,12 @@ __device__ __forceinline__ void queue_eval(const Sys &d, uint32_t code, const Ti
     const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
     long long qx, qy;
     pair_force_q(d, t.X[k], t.X[j], t.v[k], t.v[j], t.id[k], t.id[j], s_lo, s_hi, qx, qy);
-    fq_add(&t.f[2 * k], qx);
-    fq_add(&t.f[2 * k + 1], qy);
+    fq_add(&t.f[4 * k], qx);
+    fq_add(&t.f[4 * k + 2], qy);
     if (COUNT) atomicAdd(&t.cnt[k], 1u);
     if ((code >> 24) & 1u) {
-        fq_add(&t.f[2 * j], -qx);
-        fq_add(&t.f[2 * j + 1], -qy);
+        fq_add(&t.f[4 * j], -qx);
+        fq_add(&t.f[4 * j + 2], -qy);
         if (COUNT) atomicAdd(&t.cnt[j], 1u);
     }
 }
@@ -530,12 +547,12 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
         uint32_t c0 = 0, c1 = 0;
         if (have) {
             const uint2 xj = t.X[j];
-            p0 = in_range(d, r2_u(sep_u(xi.x, xj.x), sep_u(xi.y, xj.y))) & (t.id[j] != pid);
+            p0 = in_range(d, xi.x, xi.y, xj.x, xj.y) & (t.id[j] != pid);
             c0 = tag | ((uint32_t)j << 12);
             ++j;
             if (j < je) {
                 const uint2 xk = t.X[j];
-                p1 = in_range(d, r2_u(sep_u(xi.x, xk.x), sep_u(xi.y, xk.y))) & (t.id[j] != pid);
+                p1 = in_range(d, xi.x, xi.y, xk.x, xk.y) & (t.id[j] != pid);
                 c1 = tag | ((uint32_t)j << 12);
                 ++j;
             }
@@ -691,7 +708,7 @@ __device__ __forceinline__ void pairs_flat(const Sys &d, int n_own, int total, i
                 const uint32_t j = f + (uint32_t)((int)rc.w >> 13);
                 if (r >= 0 && r < 32 && j < (uint32_t)total && (rc.w & 0xfffu) < (uint32_t)n_own) {
                     const uint2 xj = t.X[j];
-                    p = in_range(d, r2_u(sep_u(rc.x, xj.x), sep_u(rc.y, xj.y))) & (t.id[j] != rc.z);
+                    p = in_range(d, rc.x, rc.y, xj.x, xj.y) & (t.id[j] != rc.z);
                     code = (rc.w & 0xfffu) | (j << 12) | (((rc.w >> 12) & 1u) << 24);
                 } else {
                     set_err_at(d, ERR_INTERNAL, 6, r, (long long)j, total);
@@ -741,7 +758,7 @@ __device__ void force_tile_global(const Sys &d, uint32_t g0, int n_own, uint32_t
                     const uint32_t idj = d.S_id[q];
                     if (idj == pid) continue;
                     const uint4 xj = d.S_xv[q];
-                    if (!in_range(d, r2_u(sep_u(xv.x, xj.x), sep_u(xv.y, xj.y)))) continue;
+                    if (!in_range(d, xv.x, xv.y, xj.x, xj.y)) continue;
                     long long qx, qy;
                     pair_force_q(d, xi, make_uint2(xj.x, xj.y), vi, make_float2(vbits(xj.z), vbits(xj.w)), idi, idj,
                                  s_lo, s_hi, qx, qy);
@@ -796,12 +813,12 @@ __device__ __forceinline__ void queue_eval_g(const Sys &d, uint32_t code, const 
     const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
     long long qx, qy;
     pair_force_q(d, t.X[k], t.X[j], t.v[k], t.v[j], t.id[k], t.id[j], s_lo, s_hi, qx, qy);
-    fq_add(&t.f[2 * k], qx);
-    fq_add(&t.f[2 * k + 1], qy);
+    fq_add(&t.f[4 * k], qx);
+    fq_add(&t.f[4 * k + 2], qy);
     if (COUNT) atomicAdd(&t.cnt[k], 1u);
     if (s_own[j]) {
-        fq_add(&t.f[2 * j], -qx);
-        fq_add(&t.f[2 * j + 1], -qy);
+        fq_add(&t.f[4 * j], -qx);
+        fq_add(&t.f[4 * j + 2], -qy);
         if (COUNT) atomicAdd(&t.cnt[j], 1u);
     }
 }
@@ -874,7 +891,7 @@ __device__ __forceinline__ void pairs_grid(const Sys &d, int n_own, int x0, int 
             c[u] = 0u;
             if (j < je) {
                 const uint2 xj = t.X[j];
-                p[u] = in_range(d, r2_u(sep_u(Xi, xj.x), sep_u(Yi, xj.y))) & (t.id[j] != pid);
+                p[u] = in_range(d, Xi, Yi, xj.x, xj.y) & (t.id[j] != pid);
                 c[u] = (uint32_t)si | ((uint32_t)j << 12);
                 ++j;
             }
@@ -908,7 +925,7 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
         unsigned char *p = smem + TP::bead_off(NT);
         t.X = (uint2 *)p;
         t.v = (float2 *)(p + 8 * (size_t)cap);
-        t.f = (long long *)(p + 16 * (size_t)cap);
+        t.f = (int *)(p + 16 * (size_t)cap);
         t.id = (uint32_t *)(p + 32 * (size_t)cap);
         t.cnt = (uint32_t *)(p + 36 * (size_t)cap);   // COUNT only
         t.lc = nullptr;
@@ -1002,8 +1019,10 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
             t.X[s] = make_uint2(xv.x, xv.y);
             t.v[s] = make_float2(vbits(xv.z), vbits(xv.w));
             t.id[s] = d.S_id[g];
-            t.f[2 * s] = 0;
-            t.f[2 * s + 1] = 0;
+            t.f[4 * s] = 0;
+            t.f[4 * s + 1] = 0;
+            t.f[4 * s + 2] = 0;
+            t.f[4 * s + 3] = 0;
             if (COUNT) t.cnt[s] = 0u;
             s_own[s] = owned ? 1 : 0;
             if (owned) s_oslot[g - g0] = (uint16_t)s;
@@ -1023,7 +1042,7 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
             const uint32_t id = t.id[s];
             if (COUNT && d.pcnt) d.pcnt[id] = t.cnt[s];
             integrate_bead<B>(d, (int)g0 + k, make_uint4(x.x, x.y, fbits(v.x), fbits(v.y)), id,
-                              fq_to_f(t.f[2 * s]), fq_to_f(t.f[2 * s + 1]), flags, th);
+                              fq_load(&t.f[4 * s]), fq_load(&t.f[4 * s + 2]), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
@@ -1126,8 +1145,10 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             t.X[k] = make_uint2(xv.x, xv.y);
             t.v[k] = make_float2(vbits(xv.z), vbits(xv.w));
             t.id[k] = d.S_id[g0 + k];
-            t.f[2 * k] = 0;
-            t.f[2 * k + 1] = 0;
+            t.f[4 * k] = 0;
+            t.f[4 * k + 1] = 0;
+            t.f[4 * k + 2] = 0;
+            t.f[4 * k + 3] = 0;
             if (COUNT) t.cnt[k] = 0u;
             t.lc[k] = (unsigned char)(lx | (ly << 4));
         }
@@ -1166,7 +1187,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             const uint4 xv = d.S_xv[g];
             const uint32_t id = t.id[k];
             if (COUNT && d.pcnt && id < (uint32_t)d.n) d.pcnt[id] = t.cnt[k];
-            integrate_bead<B>(d, g, xv, id, fq_to_f(t.f[2 * k]), fq_to_f(t.f[2 * k + 1]), flags, th);
+            integrate_bead<B>(d, g, xv, id, fq_load(&t.f[4 * k]), fq_load(&t.f[4 * k + 2]), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
