@@ -84,7 +84,8 @@ typedef struct dpd_params {
     int32_t variant;       /* pair-kernel variant: 0 = default (fastest),
                               1 = thread-per-bead, 2 = pair queue,
                               3 = grid-order pair queue, 4 = flat range
-                              enumeration.  tile = variant = 0 takes the
+                              enumeration, 5 = pair queue over merged
+                              ranges.  tile = variant = 0 takes the
                               shape dpd_autotune cached for this workload,
                               else the built-in default.  Every shape gives
                               the same trajectory bits.                     */
@@ -286,7 +287,7 @@ int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
 
 /* Kernel-shape autotuner (no counterpart in the paper: its runs used a CPU
  * molecular-dynamics code).  The cell-block side B in {4, 8, 16} and the pair
- * walk variant (1-4) only change how the step's work is cut into CTAs and
+ * walk variant (1-5) only change how the step's work is cut into CTAs and
  * lanes; all shapes give bit-identical trajectories.
  *
  * dpd_autotune creates a temporary context per shape on `stream` (device
@@ -296,7 +297,7 @@ int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
  * and keeps the better time.  The fastest shape is returned in rep and cached
  * (process-wide, thread-safe) under the key (n_beads, L, r_c); dpd_create
  * with tile = variant = 0 then uses it.  dpd_batch_autotune does the same for
- * a batch of R replicas (variants 2-4; key: R, sum of N, sum of L^2, sum of
+ * a batch of R replicas (variants 2-5; key: R, sum of N, sum of L^2, sum of
  * N^2) from dpd_batch_init_random(p[0].seed); dpd_batch_create with
  * p[0].tile = p[0].variant = 0 uses it.  Errors of a run are returned as is;
  * DPD_ERR_INVALID_ARG if no shape fits.  dpd_tune_store seeds the cache with a

@@ -137,7 +137,7 @@ int dpd_autotune(const dpd_params *p, const double *x, const float *v, int where
     Events ev;
     if (!ev.a || !ev.b) return DPD_ERR_CUDA;
     for (int ti = 0; ti < 3; ++ti)
-        for (int var = 1; var <= 4; ++var) {
+        for (int var = 1; var <= 5; ++var) {
             const int i = rep->n_shapes++;
             rep->tile[i] = TILES[ti];
             rep->variant[i] = var;
@@ -177,7 +177,7 @@ int dpd_batch_autotune(const dpd_params *p, int R, int steps, void *stream, dpd_
     if (!ev.a || !ev.b) return DPD_ERR_CUDA;
     std::vector<dpd_params> q(p, p + R);
     for (int ti = 0; ti < 3; ++ti)
-        for (int var = 2; var <= 4; ++var) {
+        for (int var = 2; var <= 5; ++var) {
             const int i = rep->n_shapes++;
             rep->tile[i] = TILES[ti];
             rep->variant[i] = var;
@@ -218,7 +218,7 @@ int dpd_batch_autotune(const dpd_params *p, int R, int steps, void *stream, dpd_
 
 int dpd_tune_store(const dpd_params *p, int R, int tile, int variant)
 {
-    if (!p || R < 1 || R > 1023 || !(tile == 4 || tile == 8 || tile == 16) || variant < 1 || variant > 4)
+    if (!p || R < 1 || R > 1023 || !(tile == 4 || tile == 8 || tile == 16) || variant < 1 || variant > 5)
         return DPD_ERR_INVALID_ARG;
     TuneEntry k = R == 1 ? single_key(p) : batch_key(p, R);
     k.tile = tile;

@@ -170,6 +170,7 @@ static int ens_dispatch_prepare(dpd_batch *b)
     if (b->var == 1) return b->B == 4 ? ens_prepare<4, 1>(b) : b->B == 8 ? ens_prepare<8, 1>(b) : ens_prepare<16, 1>(b);
     if (b->var == 3) return b->B == 4 ? ens_prepare<4, 3>(b) : b->B == 8 ? ens_prepare<8, 3>(b) : ens_prepare<16, 3>(b);
     if (b->var == 4) return b->B == 4 ? ens_prepare<4, 4>(b) : b->B == 8 ? ens_prepare<8, 4>(b) : ens_prepare<16, 4>(b);
+    if (b->var == 5) return b->B == 4 ? ens_prepare<4, 5>(b) : b->B == 8 ? ens_prepare<8, 5>(b) : ens_prepare<16, 5>(b);
     return b->B == 4 ? ens_prepare<4, 2>(b) : b->B == 8 ? ens_prepare<8, 2>(b) : ens_prepare<16, 2>(b);
 }
 
@@ -187,6 +188,10 @@ static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last)
         if (b->B == 4) ens_launch<4, 4>(b, nsteps, final_last);
         else if (b->B == 8) ens_launch<8, 4>(b, nsteps, final_last);
         else ens_launch<16, 4>(b, nsteps, final_last);
+    } else if (b->var == 5) {
+        if (b->B == 4) ens_launch<4, 5>(b, nsteps, final_last);
+        else if (b->B == 8) ens_launch<8, 5>(b, nsteps, final_last);
+        else ens_launch<16, 5>(b, nsteps, final_last);
     } else {
         if (b->B == 4) ens_launch<4, 2>(b, nsteps, final_last);
         else if (b->B == 8) ens_launch<8, 2>(b, nsteps, final_last);

@@ -196,7 +196,7 @@ int validate(const dpd_params *p)
         return DPD_ERR_INVALID_ARG;
     if (p->n_beads < 2 || (p->n_beads & 1) || p->n_beads >= (1ll << 31)) return DPD_ERR_INVALID_ARG;
     if (!(p->tile == 0 || p->tile == 4 || p->tile == 8 || p->tile == 16)) return DPD_ERR_INVALID_ARG;
-    if (p->variant < 0 || p->variant > 4) return DPD_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 5) return DPD_ERR_INVALID_ARG;
     if (p->noise < 0 || p->noise > 1) return DPD_ERR_INVALID_ARG;
     if (!(p->wexp >= 0.0 && p->wexp <= 8.0)) return DPD_ERR_INVALID_ARG;
     const int nc = n_cells_side(p->L, p->rc);
@@ -282,6 +282,13 @@ size_t force_smem(int B, int var, int cap, bool count)
             default: return TilePlan<16, 4>::bytes(cap, TILE_THREADS, count);
         }
     }
+    if (var == 5) {
+        switch (B) {
+            case 4: return TilePlan<4, 5>::bytes(cap, TILE_THREADS, count);
+            case 8: return TilePlan<8, 5>::bytes(cap, TILE_THREADS, count);
+            default: return TilePlan<16, 5>::bytes(cap, TILE_THREADS, count);
+        }
+    }
     switch (B) {
         case 4: return TilePlan<4>::bytes(cap, TILE_THREADS, count);
         case 8: return TilePlan<8>::bytes(cap, TILE_THREADS, count);
@@ -312,6 +319,8 @@ static int set_force_attrs(int smax)
     if (!rc) rc = set_dyn_limit(k_force<B, true, 3>, smax);
     if (!rc) rc = set_dyn_limit(k_force<B, false, 4>, smax);
     if (!rc) rc = set_dyn_limit(k_force<B, true, 4>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, false, 5>, smax);
+    if (!rc) rc = set_dyn_limit(k_force<B, true, 5>, smax);
     return rc;
 }
 
@@ -360,6 +369,12 @@ void launch_force_only(const Sys &d, int B, int var, cudaStream_t st, size_t sme
             case 4: launch_force_t<4, 4>(d, st, smem, flags, count); break;
             case 8: launch_force_t<8, 4>(d, st, smem, flags, count); break;
             default: launch_force_t<16, 4>(d, st, smem, flags, count); break;
+        }
+    } else if (var == 5) {
+        switch (B) {
+            case 4: launch_force_t<4, 5>(d, st, smem, flags, count); break;
+            case 8: launch_force_t<8, 5>(d, st, smem, flags, count); break;
+            default: launch_force_t<16, 5>(d, st, smem, flags, count); break;
         }
     } else {
         switch (B) {

@@ -346,7 +346,7 @@ template <int B, int VAR = 2>
 struct TilePlan {
     static constexpr int NCL = (B + 2) * (B + 2);   // local cell table
     static constexpr int NH = 4 * B + 4;            // halo cells
-    static constexpr int NITEM = VAR == 4 ? B * B * (FLAT_MAXI + 1) : 0;
+    static constexpr int NITEM = (VAR == 4 || VAR == 5) ? B * B * (FLAT_MAXI + 1) : 0;
     static constexpr int NINT = 2 * NCL + 3 * (NH + 1) + 8 + NITEM;
     static constexpr int QLEN = VAR == 4 ? 64 : 128;            // queue entries per warp
     static constexpr int WARP_BYTES = 4 * QLEN + (VAR == 4 ? 16 * 32 : 0);
@@ -722,6 +722,78 @@ __device__ __forceinline__ void pairs_flat(const Sys &d, int n_own, int total, i
         }
         b = e;
         __syncwarp();
+    }
+    __syncwarp();
+    if (lane < qn) eval(q[lane]);
+}
+
+// Variant 5: the lane walk of variant 2 over the merged candidate ranges of
+// variant 4's cell tables.  A lane holds one range of one bead; when it runs
+// out it takes the next range of its bead (or the next bead), one step per
+// round, so a bead costs about 2.3 range switches instead of one per
+// neighbour cell; every round each lane tests CPR candidates and the pairs
+// inside r_c go through the warp queue.
+template <bool COUNT, int CPR>
+__device__ __forceinline__ void pairs_items(const Sys &d, int n_own, int total, int tw, const TileArrays &t,
+                                            const int *s_nit, const uint32_t *s_items, volatile uint32_t *q,
+                                            int *s_next, uint32_t s_lo, uint32_t s_hi)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int k = 0, ii = 0, ni = 0, oc = 0;
+    uint32_t j = 0, je = 0, tag = 0, pid = 0;
+    uint2 xi = make_uint2(0u, 0u);
+    bool more = true;
+    int qn = 0;   // warp-uniform queue length
+    auto eval = [&](uint32_t code) { queue_eval<COUNT>(d, code, t, s_lo, s_hi); };
+    while (true) {
+        bool have = j < je;
+        if (!have && more) {
+            if (ii >= ni) {
+                k = atomicAdd(s_next, 1);
+                if (k >= n_own) {
+                    more = false;
+                } else {
+                    const uint32_t lc = t.lc[k];
+                    oc = (int)(lc >> 4) * tw + (int)(lc & 15u);
+                    ni = s_nit[oc];
+                    ii = 0;
+                    xi = t.X[k];
+                    pid = d.excl ? (t.id[k] ^ 1u) : 0xffffffffu;
+                }
+            }
+            if (more) {
+                const uint32_t it = s_items[oc * FLAT_MAXI + min(ii, FLAT_MAXI - 1)];
+                j = ii == 0 ? (uint32_t)k + 1u : (it & 0x1fffu);
+                je = min((it >> 13) & 0x1fffu, (uint32_t)total);
+                tag = (uint32_t)k | (((it >> 26) & 1u) << 24);
+                ++ii;
+                have = j < je;
+            }
+        }
+        if (!__any_sync(FULL, have || more)) break;
+        bool p[CPR];
+        uint32_t c[CPR];
+#pragma unroll
+        for (int u = 0; u < CPR; ++u) {
+            p[u] = false;
+            c[u] = 0u;
+            if (j < je) {
+                const uint2 xj = t.X[j];
+                p[u] = in_range(d, xi.x, xi.y, xj.x, xj.y) & (t.id[j] != pid);
+                c[u] = tag | (j << 12);
+                ++j;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CPR; ++u) {
+            const unsigned m = __ballot_sync(FULL, p[u]);
+            if (p[u]) q[qn + __popc(m & lt)] = c[u];
+            qn += __popc(m);
+        }
+        __syncwarp();
+        queue_drain<CPR>(q, qn, eval);
     }
     __syncwarp();
     if (lane < qn) eval(q[lane]);
@@ -1176,6 +1248,10 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             __syncthreads();
             pairs_flat<COUNT>(d, n_own, total, tw, t, s_nit, s_items, (uint4 *)wbuf, (uint32_t *)(wbuf + 16 * 32),
                               s_sc + 1, s_lo, s_hi);
+        } else if constexpr (VAR == 5) {
+            flat_cell_items<B>(d, tw, th_, n_own, s_cbeg, s_ccnt, s_nit, s_items);
+            __syncthreads();
+            pairs_items<COUNT, 2>(d, n_own, total, tw, t, s_nit, s_items, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi);
         } else {
             pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi);
         }

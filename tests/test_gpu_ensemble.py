@@ -39,7 +39,7 @@ def mods():
     return Ensemble, Sim
 
 
-@pytest.mark.parametrize("variant", [2, 3, 4])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
 def test_batch_matches_single_system(mods, variant):
     Ensemble, Sim = mods
     pts = [dict(p, variant=variant) for p in _points()]

@@ -69,7 +69,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("L,nd,tile,seed", CASES)
 def test_setup_force_parity(Sim, orc, L, nd, tile, seed, variant):
     x, _ = synth.dimers(nd, L, 0.5, seed=seed)
@@ -96,7 +96,7 @@ def test_gaussian_noise_and_no_exclusion(Sim, orc):
     force_check(f, fo)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("L,nd,tile,seed", CASES[:4])
 def test_cell_and_pair_counts_bit_exact(Sim, orc, L, nd, tile, seed, variant):
     x, _ = synth.dimers(nd, L, 0.5, seed=seed)
@@ -128,7 +128,7 @@ def test_cell_table_after_many_steps_multiblock_scan(Sim, orc):
             np.testing.assert_array_equal(s.cell_counts(), orc.cell_counts(xg, L, nc))
 
 
-@pytest.mark.parametrize("variant", [2, 3, 4])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
 def test_trajectory_parity_c1_100_steps(Sim, orc, variant):
     """C1: 512 dimers, L = 32, seed 0: positions after 100 steps."""
     L, nd = 32.0, 512
@@ -148,7 +148,7 @@ def test_trajectory_parity_c1_100_steps(Sim, orc, variant):
     assert rel <= 1e-3, rel
 
 
-@pytest.mark.parametrize("variant", [2, 3, 4])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
 @pytest.mark.parametrize("s", [0.5, 1.0, 3.0])
 def test_weight_exponent_force_parity(Sim, orc, s, variant):
     """Changed exponent of w (w_D = w^s, w_R = w^(s/2)): set-up forces
@@ -316,7 +316,7 @@ def test_nonfinite_state_is_reported(Sim):
         assert e.value.status == -4
 
 
-@pytest.mark.parametrize("variant", [2, 3, 4])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
 def test_overflow_path_and_capacity_growth(Sim, orc, variant):
     """All beads squeezed into a quarter of the box (density 12): tiles
     overflow shared memory and take the global-memory path, whose set-up
@@ -386,7 +386,7 @@ def test_trajectory_bit_identical_across_kernel_shapes(Sim):
     x = synth.on_grid(x % L, L)
     v = synth.velocities(2 * nd, 1.0, seed=22)
     ref = None
-    for tile, variant in [(8, 2), (8, 2), (4, 1), (16, 3), (8, 3), (4, 2), (16, 2), (8, 1), (8, 4), (4, 4), (16, 4)]:
+    for tile, variant in [(8, 2), (8, 2), (4, 1), (16, 3), (8, 3), (4, 2), (16, 2), (8, 1), (8, 4), (4, 4), (16, 4), (8, 5), (4, 5), (16, 5)]:
         with Sim(L, 2 * nd, **sim_kw(seed=3, tile=tile, variant=variant)) as s:
             s.set_positions(x, v)
             s.step(60)

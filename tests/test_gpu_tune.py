@@ -37,7 +37,7 @@ def test_single_system_tuning(mods, orc):
     L, nd = 32.0, 512
     x, v = synth.dimers(nd, L, 0.5, seed=0)
     rep = tune.autotune(L, 2 * nd, x, v, steps=5, seed=0, **PHYS)
-    _check_report(rep, 12)
+    _check_report(rep, 15)
     best = (rep["best"]["tile"], rep["best"]["variant"])
     assert tune.lookup(L, 2 * nd) == best
     with Sim(L, 2 * nd, seed=0, **PHYS) as s:          # tile = variant = 0: the tuned shape
@@ -67,7 +67,7 @@ def test_batch_tuning(mods):
     pts = [dict(PHYS, L=24.0, n_beads=600, seed=3, replica=0), dict(PHYS, L=32.5, n_beads=1800, seed=4, replica=1),
            dict(PHYS, L=17.25, n_beads=300, gamma=20.0, seed=5, replica=2)]
     rep = tune.batch_autotune(pts, steps=3)
-    _check_report(rep, 9)
+    _check_report(rep, 12)
     best = (rep["best"]["tile"], rep["best"]["variant"])
     states = []
     for shape in (None, (8, 2)):
