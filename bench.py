@@ -57,16 +57,59 @@ CONFIGS = {
     "c2": dict(L=256.0, n_beads=3 * 256 * 256, name="c2-size: L=256, density 3, 196,608 beads"),
     "c1": dict(L=32.0, n_beads=1024, name="c1: L=32, 512 dimers"),
 }
-# algorithmic ALU operations per bead-step: ~13.5 half-stencil distance tests
-# x ~8 ops + ~4.7 pairs x (Philox4x32-10 ~80 + force ~30) + bond, propulsion,
-# drag and integration
-OPS_PER_BEAD_STEP = 650.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_force<8, 0, 2> launch at
-# the 3,145,728-bead workload, one ncu capture of this build
-# (profiles/force_integrate_traffic_c3.md); None once the kernel changes
-FORCE_TRAFFIC_BYTES_C3 = 257.87e6
+# algorithmic ALU operations of one step, counted on the benchmarked state:
+# OPS_TEST per half-stencil distance test (candidate pair), OPS_PAIR per
+# interacting pair (Philox4x32-10 ~80 + pair force ~30), OPS_BEAD per bead
+# (bond, propulsion, drag, two half kicks, drift, binning)
+OPS_TEST, OPS_PAIR, OPS_BEAD = 8.0, 110.0, 70.0
 BYTES_PER_BEAD_STEP = 36.0     # algorithmic HBM bytes per bead-step (read 20, write 16)
-N_SM, LANES = 152, 128
+LANES = 128                    # FP32/INT32 lanes per SM
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "force_traffic_c3.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1310_0998_gb300", "csrc", f)
+                  for f in ("sim_kernels.cuh", "dpd_device.cuh", "sim.cu")]
+
+
+def sm_count() -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(tile: int, variant: int):
+    """DRAM bytes per force-kernel launch from the committed ncu summary, if
+    it was taken on this exact kernel source and shape; else None."""
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_PROFILE):
+        if line.startswith("- ") and ": " in line:
+            k, v = line[2:].split(": ", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    try:
+        if kv.get("source_sha256_16") != kernel_source_hash():
+            return None
+        if int(kv["tile"]) != tile or int(kv["variant"]) != variant:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic_ops(counts: np.ndarray, pairs: int, n_beads: int):
+    """Candidates of the forward half stencil (own cell after the bead, E, NE,
+    N, NW) from the cell populations, the interacting pairs, and the step's
+    algorithmic operation count."""
+    n = counts.astype(np.float64)
+    fwd = np.roll(n, -1, 1) + np.roll(np.roll(n, -1, 1), -1, 0) + np.roll(n, -1, 0) + np.roll(np.roll(n, 1, 1), -1, 0)
+    cand = float((n * (n - 1.0) / 2.0).sum() + (n * fwd).sum())
+    return cand, OPS_TEST * cand + OPS_PAIR * pairs + OPS_BEAD * n_beads
 
 
 def peaks():
@@ -146,19 +189,24 @@ def cpu_oracle_rate(L, n_beads, budget_s=12.0, seed=0):
     return rate, oracle.num_threads(), f"{steps} steps of the FP64 cell-list oracle on a {n_beads}-bead box (L={L:g}, density 3), {t2 - t0:.1f} s"
 
 
-def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0):
+def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0, seq_steps=500):
     """C4: R replicas drawn from the uneven distribution (box side U(32, 192),
     area fraction U(0.05, 0.6), gamma log-U(0.5, 50), zeta log-U(0.005, 2),
-    f_p U(0.5, 2)).  Times `steps` steps of the batched persistent kernel and
-    the same steps run replica by replica through the single-system path."""
+    f_p U(0.5, 2)).  The kernel shape is tuned for this replica mix (unless
+    given), then `steps` steps of the batched persistent kernel are timed, and
+    `seq_steps` steps of every replica run alone through the single-system
+    path (scaled to `steps`: the per-step cost of a replica is steady)."""
     import torch
-    from paper_1310_0998_gb300 import Ensemble, synth
+    from paper_1310_0998_gb300 import Ensemble, synth, tune
     pts = []
     for r, e in enumerate(synth.ensemble_points(R, seed)):
         pts.append(dict(a=PHYS["a"], kBT=PHYS["kBT"], rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"],
                         dt=PHYS["dt"], L=e["L"], n_beads=2 * e["n_dimers"], gamma=e["gamma"], zeta=e["zeta"],
                         f_p=e["fp"], seed=seed + r, replica=r, variant=variant, tile=tile))
     beads = sum(p["n_beads"] for p in pts)
+    tuning = None
+    if variant == 0 and tile == 0:
+        tuning = tune.batch_autotune(pts, steps=5)
     ens = Ensemble(pts)
     ens.init_random(seed)
     ens.step(warmup)
@@ -175,17 +223,24 @@ def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0):
         v.sync()
     t0 = time.perf_counter()
     for v in views:
-        v.step(steps)
+        v.step(seq_steps)
     for v in views:
         v.sync()
-    t_seq = time.perf_counter() - t0
+    t_seq = (time.perf_counter() - t0) * steps / seq_steps
     info = ens.info()
+    shape = views[0].info()
     ens.close()
-    return {"replicas": R, "beads": beads, "steps": steps, "batched_ms_per_step": 1e3 * t_batch / steps,
-            "sequential_ms_per_step": 1e3 * t_seq / steps, "speedup": t_seq / t_batch,
-            "batched_particle_steps_per_s": beads * steps / t_batch, "grid": info["grid"],
-            "work_tiles": info["work_tiles"],
-            "timing": "wall clock around each leg, synchronised; sequential = each replica alone, one after another"}
+    out = {"replicas": R, "beads": beads, "steps": steps, "batched_s": t_batch,
+           "batched_ms_per_step": 1e3 * t_batch / steps, "sequential_ms_per_step": 1e3 * t_seq / steps,
+           "sequential_steps_timed": seq_steps, "speedup": t_seq / t_batch,
+           "batched_particle_steps_per_s": beads * steps / t_batch, "grid": info["grid"],
+           "work_tiles": info["work_tiles"], "tile": shape.tile, "variant": shape.variant,
+           "timing": "wall clock around each synchronised leg; batched: the full step count in one persistent "
+                     "launch per call; sequential: each replica alone, one after another, for "
+                     f"{seq_steps} steps, scaled to {steps}"}
+    if tuning is not None:
+        out["tuning"] = tuning
+    return out
 
 
 def observables_leg(sim, nb, reps=5):
@@ -237,7 +292,7 @@ def three_d_leg(steps=20, warmup=3, L=64.0, seed=0):
         dt = time.perf_counter() - t0
     rate = nb * steps / dt
     pk = peaks()
-    alu_peak = N_SM * LANES * pk["sm_max_mhz"] * 1e6
+    alu_peak = sm_count() * LANES * pk["sm_max_mhz"] * 1e6
     return {"beads": nb, "L": L, "steps": steps, "particle_steps_per_s": rate, "ms_per_step": 1e3 * dt / steps,
             "roofline": {"bound": "alu", "achieved": OPS_PER_BEAD_STEP_3D * rate / 1e12, "peak": alu_peak / 1e12,
                          "unit": "Tops/s", "frac": OPS_PER_BEAD_STEP_3D * rate / alu_peak},
@@ -358,11 +413,14 @@ def main():
     ap.add_argument("--no-obs", action="store_true", help="skip the observables leg")
     ap.add_argument("--wexp", type=float, default=0.0,
                     help="exponent s of w in the dissipative/random forces (0 = 2, the printed form)")
-    ap.add_argument("--variant", type=int, default=0, help="pair kernel: 0 default, 1 thread-per-bead, 2 queue, 3 grid-order queue")
-    ap.add_argument("--tile", type=int, default=0, help="cell-block side: 0 default, 4, 8, 16")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="pair kernel: 0 tuned, 1 thread-per-bead, 2 queue, 3 grid-order queue, 4 flat ranges, "
+                         "5 queue over merged ranges")
+    ap.add_argument("--tile", type=int, default=0, help="cell-block side: 0 tuned, 4, 8, 16")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--ens-replicas", type=int, default=256)
-    ap.add_argument("--ens-steps", type=int, default=20)
+    ap.add_argument("--ens-steps", type=int, default=10000)
+    ap.add_argument("--ens-seq-steps", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = CONFIGS[args.config]
@@ -384,14 +442,22 @@ def main():
     L, nb = cfg["L"], cfg["n_beads"]
     stream = torch.cuda.Stream(device=dev)
     x, v = synth.dimers(nb // 2, L, PHYS["r0"], seed=rank)
-    sim = Sim(L, nb, stream=stream.cuda_stream, seed=rank, a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"],
-              rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"],
-              dt=PHYS["dt"], mass=PHYS["mass"], variant=args.variant, tile=args.tile, wexp=args.wexp)
+    phys = dict(a=PHYS["a"], gamma=PHYS["gamma"], kBT=PHYS["kBT"], rc=PHYS["rc"], k_bond=PHYS["kbond"],
+                r0=PHYS["r0"], f_p=PHYS["fp"], zeta=PHYS["zeta"], dt=PHYS["dt"], mass=PHYS["mass"], wexp=args.wexp)
+    tuning = None
+    if args.variant == 0 and args.tile == 0:
+        # kernel shape: every (cell-block side, pair walk) timed on this
+        # workload; the context below takes the fastest (all shapes give the
+        # same trajectory bits)
+        from paper_1310_0998_gb300 import tune
+        tuning = tune.autotune(L, nb, x, v, steps=5, stream=stream.cuda_stream, seed=rank, **phys)
+    sim = Sim(L, nb, stream=stream.cuda_stream, seed=rank, variant=args.variant, tile=args.tile, **phys)
     sim.set_positions(x, v)
-    for _ in range(args.warmup):
-        sim.step(1)
+    sim.step(args.warmup)
     sim.sync()
+    counts = sim.cell_counts()
     _, npairs = sim.pair_counts()
+    n_cand, ops_step = algorithmic_ops(counts, int(npairs), nb)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)     # 512 MiB
     sink = torch.zeros(1, dtype=torch.float32, device=dev)
 
@@ -404,26 +470,31 @@ def main():
     try:
         pr = torch.cuda.get_device_properties(dev)
         bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        n_sm = int(pr.multi_processor_count)
     except Exception:
-        bus = None
+        bus, n_sm = None, 152
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # the K timed steps are one library call (CUDA graphs of 8 steps and a
+    # final step that also writes the canonical state), bracketed by events on
+    # the simulator's stream; every step touches ~200 MB (> the 129 MB L2).
+    # The clock sampler starts 0.6 s of untimed steps before the timed region
+    # so that it sees the GPU under this load whatever K is.
     clocks = Clocks(bus)
-    evs = []
-    for k in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.step(1)
-        e1.record(stream)
-        evs.append((e0, e1))
-        l2_flush(k)
+    t_pre = time.perf_counter()
+    while time.perf_counter() - t_pre < 0.6:
+        sim.step(64)
+        sim.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     sim.sync()
-    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
-    t_dev = max_over_ranks(float(step_ms.sum()) / 1e3, world, dev)
+    t_dev = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
     if world > 1:
         dist.barrier()
     value = job_throughput(world, nb, args.steps, t_dev)
@@ -455,9 +526,11 @@ def main():
     info = sim.info()
 
     pk = peaks()
-    alu_peak = N_SM * LANES * pk["sm_max_mhz"] * 1e6
-    alu_ach = OPS_PER_BEAD_STEP * nb / force_s
+    alu_peak = n_sm * LANES * pk["sm_max_mhz"] * 1e6
+    alu_ach = ops_step / force_s
     hbm_ach = BYTES_PER_BEAD_STEP * value / world / 1e9
+    traffic = measured_traffic(info.tile, info.variant) if cfg["name"].startswith("c3") and args.wexp in (0.0, 2.0) \
+        else None
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
@@ -465,13 +538,19 @@ def main():
         "data": "synthetic",
         "config": {"workload": cfg["name"], "beads": nb, "L": L, "bead_density": nb / L / L,
                    "tile": info.tile, "variant": info.variant, "wexp": args.wexp if args.wexp > 0 else 2.0,
-                   "l2": "512 MiB write+read flush between timed steps",
-                   "pairs_per_bead": npairs / nb, "parallelism": "replicas" if world > 1 else "single"},
+                   "l2": "inputs larger than L2: every step reads and writes ~200 MB of state (L2 129 MB)",
+                   "pairs_per_bead": npairs / nb, "candidates_per_bead": n_cand / nb,
+                   "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "force_integrate", "achieved": alu_ach / 1e12,
-                     "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": (FORCE_TRAFFIC_BYTES_C3 if cfg["name"].startswith("c3") and info.tile == 8
-                                 and info.variant == 2 and args.wexp in (0.0, 2.0) else None),
-                     "traffic_unit": "bytes per launch (ncu, final step of a call)",
-                     "peak_src": f"{N_SM} SMs x {LANES} lanes x {pk['sm_max_mhz']:.0f} MHz",
+                     "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": alu_ach / alu_peak, "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per launch (ncu, body step of a multi-step call; null unless "
+                                     "profiles/force_traffic_c3.md was taken on this kernel source and shape)",
+                     "traffic_per_bead": traffic / nb if traffic else None,
+                     "ops_per_bead_step": ops_step / nb,
+                     "ops_model": f"{OPS_TEST:g} x candidate tests + {OPS_PAIR:g} x pairs + {OPS_BEAD:g} x beads, "
+                                  "counted on the benchmarked state",
+                     "peak_src": f"{n_sm} SMs x {LANES} lanes x {pk['sm_max_mhz']:.0f} MHz (max SM clock, "
+                                 f"{pk['src']} peaks file)",
                      "ms": force_s * 1e3},
         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm"], "frac": hbm_ach / pk["hbm"],
                 "bytes_per_bead_step": BYTES_PER_BEAD_STEP, "peak_src": pk["src"]},
@@ -483,9 +562,11 @@ def main():
         "overflow_tiles": int(info.overflow_tiles),
         "clocks": clk,
     }
+    if tuning is not None:
+        line["tuning"] = tuning
     if rank == 0 and not args.no_ensemble:
         line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup, variant=args.variant,
-                                        tile=args.tile)
+                                        tile=args.tile, seq_steps=min(args.ens_seq_steps, args.ens_steps))
     if rank == 0 and not args.no_surrogate:
         line["surrogate"] = surrogate_leg()
     if rank == 0 and not args.no_obs:
