@@ -220,7 +220,11 @@ int dpd_vorticity(dpd_ctx *ctx, int M, double eps, double *omega);
  * L_int = trapezoid of g over r = 0 (g = 1) and the non-empty bin centres.
  * Host outputs: g [nbins] (NaN for empty bins or a zero denominator), L_int
  * (may be NULL), num [nbins] pair sums and cnt [nbins] pair counts (either
- * may be NULL).  O(N_agents^2) pair pass on the device.  Synchronises. */
+ * may be NULL).  Pair pass on the device over the agent pairs within
+ * r_max = nbins dr: a periodic cell grid of side >= r_max when at least three
+ * such cells fit per side (O(N_agents rho r_max^2) work), else all agent
+ * pairs (O(N_agents^2)); counts and sums are the same either way (FP64
+ * minimum image, shells, products).  Synchronises. */
 int dpd_velocity_correlation(dpd_ctx *ctx, double dr, int nbins, double *g, double *L_int,
                              double *num, int64_t *cnt);
 

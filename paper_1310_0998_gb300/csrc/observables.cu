@@ -246,6 +246,160 @@ __global__ void __launch_bounds__(VCF_TILE) k_vcf(const double2 *c, const double
     }
 }
 
+// ---- velocity correlation limited to r < r_max = nbins dr ------------------
+// Agents are counting-sorted into a periodic grid of ncv x ncv cells of side
+// L / ncv >= r_max, so every pair inside r_max lies in the same or an
+// adjacent cell.  One block per cell takes its own agents against the agents
+// of the cell itself (b after a) and of its four forward neighbours (E, NE,
+// N, NW), each neighbour cell staged in shared memory in chunks.  Separations
+// are taken in FP32 from offsets to the block's cell corner (error below
+// 1e-5); a pair whose r / dr lies within 1e-3 of a shell edge or of r_max is
+// decided by the FP64 expressions of k_vcf instead, so the shell of every
+// pair, and hence the counts, equal the all-pairs kernel's; the products
+// v_a . v_b are FP64 as there.
+constexpr int VCFC_THREADS = 128, VCFC_CHUNK = 512, VCFC_WARPS = VCFC_THREADS / 32;
+
+__device__ __forceinline__ int vcf_cell_of(double x, double cw, int ncv)
+{
+    const int c = (int)floor(__ddiv_rn(x, cw));
+    return c < 0 ? 0 : (c >= ncv ? ncv - 1 : c);
+}
+
+__global__ void k_vcf_count(const double2 *c, int na, double cw, int ncv, unsigned *cnt, unsigned *rank)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const double2 p = c[k];
+    const int cell = vcf_cell_of(p.y, cw, ncv) * ncv + vcf_cell_of(p.x, cw, ncv);
+    rank[k] = atomicAdd(&cnt[cell], 1u);
+}
+
+// Exclusive scan of n counts in one block (n up to a few million): each
+// thread sums a contiguous run, a block scan of the run sums, then the runs.
+__global__ void k_vcf_scan(const unsigned *cnt, int n, unsigned *start)
+{
+    __shared__ unsigned s_sum[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int per = (n + T - 1) / T, b = t * per, e = min(n, b + per);
+    unsigned sum = 0;
+    for (int i = b; i < e; ++i) sum += cnt[i];
+    s_sum[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        const unsigned v = t >= o ? s_sum[t - o] : 0u;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    unsigned run = s_sum[t] - sum;
+    for (int i = b; i < e; ++i) {
+        start[i] = run;
+        run += cnt[i];
+    }
+    if (t == T - 1) start[n] = s_sum[t];
+}
+
+__global__ void k_vcf_scatter(const double2 *c, const double2 *v, int na, double cw, int ncv, const unsigned *start,
+                              const unsigned *rank, double2 *sc, double2 *sv)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const double2 p = c[k];
+    const int cell = vcf_cell_of(p.y, cw, ncv) * ncv + vcf_cell_of(p.x, cw, ncv);
+    const unsigned dst = start[cell] + rank[k];
+    if (dst < (unsigned)na) {
+        sc[dst] = p;
+        sv[dst] = v[k];
+    }
+}
+
+__global__ void __launch_bounds__(VCFC_THREADS) k_vcf_cells(const double2 *sc, const double2 *sv,
+                                                            const unsigned *start, int ncv, double L, double cw,
+                                                            double dr, int nbins, double *gnum,
+                                                            unsigned long long *gcnt)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *snum = (double *)smem;                                          // [VCFC_WARPS][nbins]
+    unsigned long long *scnt = (unsigned long long *)(snum + VCFC_WARPS * nbins);
+    double2 *bc = (double2 *)(scnt + VCFC_WARPS * nbins);                   // [VCFC_CHUNK]
+    double2 *bv = bc + VCFC_CHUNK;
+    float2 *bo = (float2 *)(bv + VCFC_CHUNK);
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < VCFC_WARPS * nbins; i += blockDim.x) { snum[i] = 0.0; scnt[i] = 0ull; }
+    const int cell = blockIdx.x, cy = cell / ncv, cx = cell - cy * ncv;
+    const unsigned a0 = start[cell], a1 = start[cell + 1];
+    const double ox = cx * cw, oy = cy * cw, hL = 0.5 * L;
+    const double rmax2 = (double)nbins * dr * (double)nbins * dr * (1.0 + 1e-9);
+    const float rscr = (float)(nbins * dr) * 1.0001f + 1e-4f * (float)cw, rscr2 = rscr * rscr;
+    const float inv_drf = (float)(1.0 / dr), nbf = (float)nbins;
+    double *wnum = snum + warp * nbins;
+    unsigned long long *wcnt = scnt + warp * nbins;
+    for (int nb = 0; nb < 5; ++nb) {
+        // own cell, then E, NE, N, NW; periodic images carry their shift
+        const int dxc = nb == 0 ? 0 : (nb <= 2 ? 1 : (nb == 3 ? 0 : -1));
+        const int dyc = nb <= 1 ? 0 : 1;
+        int nx = cx + dxc, ny = cy + dyc;
+        double sx = 0.0, sy = 0.0;
+        if (nx >= ncv) { nx -= ncv; sx = L; } else if (nx < 0) { nx += ncv; sx = -L; }
+        if (ny >= ncv) { ny -= ncv; sy = L; }
+        const int nc = ny * ncv + nx;
+        const unsigned b0 = start[nc], b1 = start[nc + 1];
+        for (unsigned c0 = b0; c0 < b1; c0 += VCFC_CHUNK) {
+            const int m = (int)min((unsigned)VCFC_CHUNK, b1 - c0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                const double2 p = sc[c0 + q];
+                bc[q] = p;
+                bv[q] = sv[c0 + q];
+                bo[q] = make_float2((float)(p.x + sx - ox), (float)(p.y + sy - oy));
+            }
+            __syncthreads();
+            for (unsigned a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                const double2 ca = sc[a], va = sv[a];
+                const float ax = (float)(ca.x - ox), ay = (float)(ca.y - oy);
+                const int q0 = nb == 0 ? (int)max(0ll, (long long)a + 1 - (long long)c0) : 0;
+                for (int q = q0; q < m; ++q) {
+                    const float fx = ax - bo[q].x, fy = ay - bo[q].y;
+                    const float r2f = fx * fx + fy * fy;
+                    if (r2f >= rscr2) continue;
+                    // the shell from the FP32 separation (error below 1e-5)
+                    // wherever r / dr lies at least 1e-3 from a shell edge
+                    // and from r_max; otherwise the FP64 expressions of k_vcf
+                    const float tf = sqrtf(r2f) * inv_drf;
+                    const float fl = floorf(tf);
+                    int bin;
+                    if (tf - fl > 1e-3f && fl + 1.0f - tf > 1e-3f && tf < nbf - 1e-3f) {
+                        bin = (int)fl;
+                    } else {
+                        const double2 cb = bc[q];
+                        double dx = __dsub_rn(ca.x, cb.x), dy = __dsub_rn(ca.y, cb.y);
+                        dx = dx > hL ? __dsub_rn(dx, L) : (dx < -hL ? __dadd_rn(dx, L) : dx);
+                        dy = dy > hL ? __dsub_rn(dy, L) : (dy < -hL ? __dadd_rn(dy, L) : dy);
+                        const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                        if (!(r2 < rmax2)) continue;
+                        const double bf = floor(__ddiv_rn(sqrt(r2), dr));
+                        if (!(bf < (double)nbins)) continue;
+                        bin = (int)bf;
+                    }
+                    const double2 vb = bv[q];
+                    atomicAdd(&wnum[bin], __dadd_rn(__dmul_rn(va.x, vb.x), __dmul_rn(va.y, vb.y)));
+                    atomicAdd(&wcnt[bin], 1ull);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        double sn = 0.0;
+        unsigned long long cn = 0ull;
+        for (int w = 0; w < VCFC_WARPS; ++w) { sn += snum[w * nbins + b]; cn += scnt[w * nbins + b]; }
+        if (cn) {
+            atomicAdd(&gnum[b], sn);
+            atomicAdd(&gcnt[b], cn);
+        }
+    }
+}
+
 }  // namespace dpd
 
 using namespace dpd;
@@ -386,25 +540,53 @@ int dpd_velocity_correlation(dpd_ctx *c, double dr, int nbins, double *g, double
     if (!c || !g || !(dr > 0) || nbins < 1 || nbins > 8192) return DPD_ERR_INVALID_ARG;
     if (!c->have_state) return DPD_ERR_STATE;
     const int na = c->d.n / 2;
-    const size_t bytes = 32 * (size_t)na + 16 * (size_t)nbins + 64;
+    const double L = c->p.L;
+    // pairs within r_max = nbins dr only: a cell grid of side >= r_max when at
+    // least three cells fit per side (and the grid stays below 4 M cells),
+    // else all pairs; both evaluate a pair with the same arithmetic
+    const double rmax = (double)nbins * dr * (1.0 + 1e-9);
+    const double ncv_d = std::floor(L / rmax);
+    const bool cells = ncv_d >= 3.0 && ncv_d <= 2048.0;
+    const int ncv = cells ? (int)ncv_d : 0, ncell = ncv * ncv;
+    const size_t a256 = 256;
+    auto up = [&](size_t x) { return (x + a256 - 1) & ~(a256 - 1); };
+    const size_t o_cc = 0, o_vv = up(o_cc + 16 * (size_t)na), o_num = up(o_vv + 16 * (size_t)na),
+                 o_cnt = up(o_num + 8 * (size_t)nbins), o_acc = up(o_cnt + 8 * (size_t)nbins),
+                 o_ccnt = up(o_acc + 64), o_cst = up(o_ccnt + 4 * (size_t)ncell),
+                 o_rnk = up(o_cst + 4 * ((size_t)ncell + 1)), o_scs = up(o_rnk + (cells ? 4 * (size_t)na : 0)),
+                 o_svs = up(o_scs + (cells ? 16 * (size_t)na : 0)), bytes = up(o_svs + (cells ? 16 * (size_t)na : 0));
     ObsScratch *s = scratch_of(c, bytes);
     if (!s) return DPD_ERR_OOM;
     char *b = (char *)s->buf;
-    double2 *cc = (double2 *)b; b += 16 * (size_t)na;
-    double2 *vv = (double2 *)b; b += 16 * (size_t)na;
-    double *gnum = (double *)b; b += 8 * (size_t)nbins;
-    unsigned long long *gcnt = (unsigned long long *)b; b += 8 * (size_t)nbins;
-    double *acc = (double *)b;
-    const double L = c->p.L;
-    CUO(cudaMemsetAsync(gnum, 0, 16 * (size_t)nbins + 32, c->st));
+    double2 *cc = (double2 *)(b + o_cc), *vv = (double2 *)(b + o_vv);
+    double *gnum = (double *)(b + o_num);
+    unsigned long long *gcnt = (unsigned long long *)(b + o_cnt);
+    double *acc = (double *)(b + o_acc);
+    CUO(cudaMemsetAsync(gnum, 0, 8 * (size_t)nbins, c->st));
+    CUO(cudaMemsetAsync(gcnt, 0, 8 * (size_t)nbins, c->st));
+    CUO(cudaMemsetAsync(acc, 0, 64, c->st));
     k_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->d.C_xv, na, L, c->d.ulen_d, cc, vv);
     k_vmeans<<<64, 256, 0, c->st>>>(vv, na, acc);
-    const int ntile = (na + VCF_TILE - 1) / VCF_TILE;
-    const long long nblk = (long long)ntile * (ntile + 1) / 2;
-    const size_t sm = 16 * (size_t)nbins + 32 * VCF_TILE;
-    if (sm > 200 * 1024 || nblk > 2147483647ll) return DPD_ERR_INVALID_ARG;
-    CUO(cudaFuncSetAttribute(k_vcf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_vcf<<<(unsigned)nblk, VCF_TILE, sm, c->st>>>(cc, vv, na, L, dr, nbins, gnum, gcnt);
+    if (cells) {
+        const double cw = L / ncv;
+        unsigned *ccnt = (unsigned *)(b + o_ccnt), *cst = (unsigned *)(b + o_cst), *rnk = (unsigned *)(b + o_rnk);
+        double2 *scs = (double2 *)(b + o_scs), *svs = (double2 *)(b + o_svs);
+        CUO(cudaMemsetAsync(ccnt, 0, 4 * (size_t)ncell, c->st));
+        k_vcf_count<<<(na + 255) / 256, 256, 0, c->st>>>(cc, na, cw, ncv, ccnt, rnk);
+        k_vcf_scan<<<1, 1024, 0, c->st>>>(ccnt, ncell, cst);
+        k_vcf_scatter<<<(na + 255) / 256, 256, 0, c->st>>>(cc, vv, na, cw, ncv, cst, rnk, scs, svs);
+        const size_t sm = (size_t)VCFC_WARPS * nbins * 16 + (size_t)VCFC_CHUNK * 40;
+        if (sm > 200 * 1024) return DPD_ERR_INVALID_ARG;
+        CUO(cudaFuncSetAttribute(k_vcf_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_vcf_cells<<<ncell, VCFC_THREADS, sm, c->st>>>(scs, svs, cst, ncv, L, cw, dr, nbins, gnum, gcnt);
+    } else {
+        const int ntile = (na + VCF_TILE - 1) / VCF_TILE;
+        const long long nblk = (long long)ntile * (ntile + 1) / 2;
+        const size_t sm = 16 * (size_t)nbins + 32 * VCF_TILE;
+        if (sm > 200 * 1024 || nblk > 2147483647ll) return DPD_ERR_INVALID_ARG;
+        CUO(cudaFuncSetAttribute(k_vcf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_vcf<<<(unsigned)nblk, VCF_TILE, sm, c->st>>>(cc, vv, na, L, dr, nbins, gnum, gcnt);
+    }
     CUO(cudaGetLastError());
     std::vector<double> hn(nbins), ha(3);
     std::vector<unsigned long long> hc(nbins);

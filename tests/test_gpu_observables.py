@@ -59,7 +59,10 @@ def test_explicit_filter_width_and_uniform_field(Sim):
     assert np.abs(E).max() < 1e-20
 
 
-@pytest.mark.parametrize("L,nd,dr,nbins", [(32.0, 512, 0.25, 64), (50.0, 4000, 0.5, 50)])
+@pytest.mark.parametrize("L,nd,dr,nbins", [
+    (32.0, 512, 0.25, 64), (50.0, 4000, 0.5, 50),          # r_max >= L/3: all agent pairs
+    (64.0, 6000, 0.25, 32), (30.0, 1350, 0.25, 40),         # cell grid of 8 x 8 and of 3 x 3 cells
+    (100.0, 15000, 0.3, 33)])                                # 10 x 10 cells, r_max not a cell multiple
 def test_velocity_correlation(Sim, L, nd, dr, nbins):
     x, v = _state(L, nd, 4)
     with Sim(L, 2 * nd) as s:
@@ -103,3 +106,32 @@ def test_vorticity(Sim, L, nd, M, eps):
     oo = ob.vorticity(uo, L)
     np.testing.assert_allclose(om, oo, rtol=1e-9, atol=1e-10 * np.abs(oo).max())
     assert abs(om.sum()) < 1e-9 * np.abs(om).sum()
+
+
+def test_velocity_correlation_full_size(Sim):
+    """C3 geometry (1,572,864 agents), r < 16 (64 bins of 0.25), which takes
+    the cell-grid pass.  The FP64 all-pairs reference is infeasible at this
+    size, so the counts of the first 8 bins (r < 2, about 1.5e7 pairs) are
+    checked against an exact CPU count of the same shells (a periodic k-d
+    tree finds the candidate pairs; the shell of each comes from the same
+    FP64 expressions), and the sums of those bins against the products of
+    the same pairs."""
+    spatial = pytest.importorskip("scipy.spatial")
+    L, nd = 1024.0, 3 * 1024 * 1024 // 2
+    x, v = _state(L, nd, 3)
+    with Sim(L, 2 * nd) as s:
+        s.set_positions(x, v)
+        g, Li, num, cnt = s.velocity_correlation(0.25, 64)
+    c, vc = ob.agent_com(x, v, L)
+    pairs = spatial.cKDTree(c, boxsize=L).query_pairs(2.0 + 1e-6, output_type="ndarray")
+    d = c[pairs[:, 0]] - c[pairs[:, 1]]
+    d -= L * np.rint(d / L)
+    r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+    b = np.floor(np.sqrt(r2) / 0.25)
+    keep = b < 8
+    bins = b[keep].astype(np.int64)
+    dots = (vc[pairs[keep, 0]] * vc[pairs[keep, 1]]).sum(-1)
+    np.testing.assert_array_equal(cnt[:8], np.bincount(bins, minlength=8)[:8])
+    np.testing.assert_allclose(num[:8], np.bincount(bins, weights=dots, minlength=8)[:8], rtol=1e-9,
+                               atol=1e-9 * np.abs(dots).sum())
+    assert np.all(cnt > 0) and np.isfinite(Li)
