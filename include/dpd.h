@@ -390,8 +390,8 @@ int sur_train(sur_ctx *s, const float *X, const float *Y, int n, int epochs, int
  * returns DPD_ERR_TIMEOUT. */
 int sur_predict(sur_ctx *s, const float *X, int n, float *Y, float *spread);
 
-/* Forward products of prediction on tcgen05 (1, default) or on warp-level
- * mma.sync (0); training always uses the latter. */
+/* Matrix products on tcgen05 (1, default: training products and the fused
+ * forward pass of prediction) or on warp-level mma.sync (0). */
 int sur_set_backend(sur_ctx *s, int use_tcgen05);
 
 /* Device time of `reps` forward passes of every member over the first n rows

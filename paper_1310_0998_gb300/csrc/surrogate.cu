@@ -533,6 +533,124 @@ __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat1
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
 }
 
+// The training products on the tensor cores: the same C = A B^T and
+// epilogues as k_gemm, one CTA (4 warps) per 128-row tile of C with all N <= 256
+// columns in tensor memory.  K is taken in chunks of GT_KC: every thread
+// stages its share of the A and B chunks (rows past M or N as zeros) in the
+// K-major no-swizzle layout, one thread issues the chunk's tcgen05.mma
+// instructions and commits to the mbarrier, and all wait for it (bounded)
+// before the buffers are refilled.  The epilogue reads the accumulator back
+// with tcgen05.ld, warp w holding rows 32w..32w+31, and applies the same
+// per-element arithmetic as k_gemm (expf-based SiLU), so the two backends
+// differ only in the order of the FP32 accumulation.
+constexpr int GT_KC = 64, GT_THREADS = 128;
+
+__device__ __forceinline__ void stage_chunk(unsigned char *dst, const __nv_bfloat16 *src, int r0, int rows, int nvalid,
+                                            int k0, int K)
+{
+    constexpr int ncm = GT_KC / 8;
+    for (int q = threadIdx.x; q < rows * ncm; q += blockDim.x) {
+        const int r = q / ncm, c = q - r * ncm;
+        const int gr = r0 + r, gk = k0 + 8 * c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < nvalid && gk < K) v = *reinterpret_cast<const uint4 *>(src + (size_t)gr * K + gk);
+        *reinterpret_cast<uint4 *>(dst + ((r >> 3) * ncm + c) * 128 + (r & 7) * 16) = v;
+    }
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 1) k_gemm_tc(const __nv_bfloat16 *__restrict__ A,
+                                                           const __nv_bfloat16 *__restrict__ B, int M, int N, int K,
+                                                           int epi, const float *__restrict__ bias,
+                                                           const float *__restrict__ gateZ, float *__restrict__ C32,
+                                                           __nv_bfloat16 *__restrict__ C16,
+                                                           __nv_bfloat16 *__restrict__ C16T, int tcols, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int Np = (N + 15) & ~15;
+    unsigned char *sa = sm, *sb = sm + TC_M * GT_KC * 2;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + (size_t)Np * GT_KC * 2);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M;
+    const uint32_t mb = smem_u32(mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)),
+                     "r"(tcols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc_idesc(TC_M, Np), sbo = (uint32_t)(GT_KC / 8) * 128u;
+    uint32_t parity = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < K && ok; k0 += GT_KC) {
+        stage_chunk(sa, A, m0, TC_M, M, k0, K);
+        stage_chunk(sb, B, 0, Np, N, k0, K);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int nks = min(GT_KC, K - k0) >> 4;
+            for (int ks = 0; ks < nks; ++ks) {
+                const uint64_t ad = tc_desc(smem_u32(sa) + ks * 256, 128, sbo);
+                const uint64_t bd = tc_desc(smem_u32(sb) + ks * 256, 128, sbo);
+                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mb)
+                         : "memory");
+        }
+        if (__syncthreads_or(tc_wait(mb, parity) ? 0 : 1)) {
+            ok = false;
+            if (tid == 0) atomicOr(err, 1);
+            tc_wait(mb, parity);   // second bounded wait for MMAs still in flight
+        }
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (ok) {
+        const int r = m0 + 32 * warp + lane;
+        const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            uint32_t u[16];
+            tmem_ld16_issue(tb + (uint32_t)c0, u);
+            tmem_wait(u);
+            if (r >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = c0 + j;
+                if (c >= N) break;
+                float v = __uint_as_float(u[j]);
+                const size_t o = (size_t)r * N + c;
+                if (epi == EPI_F32) {
+                    C32[o] = v;
+                } else if (epi == EPI_BIAS) {
+                    C32[o] = v + bias[c];
+                } else if (epi == EPI_BIAS_SILU) {
+                    v += bias[c];
+                    C32[o] = v;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(silu(v));
+                    C16[o] = h;
+                    C16T[(size_t)c * M + r] = h;
+                } else {   // EPI_GATE
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v * dsilu(gateZ[o]));
+                    C16[o] = h;
+                    C16T[(size_t)c * M + r] = h;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tcols) : "memory");
+}
+
 struct Member {
     float *w[3], *b[3];                 // FP32 masters
     float *mw[3], *vw[3], *mb[3], *vb[3];
@@ -570,9 +688,24 @@ static const int DIMS_OUT[3] = {NH, NH, NOUT_P};
         if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? DPD_ERR_OOM : DPD_ERR_CUDA; \
     } while (0)
 
+static size_t gemm_tc_smem(int N) { return (size_t)TC_M * GT_KC * 2 + (size_t)((N + 15) & ~15) * GT_KC * 2 + 16; }
+
+// C = A B^T on the backend in use: tcgen05 (the default) or warp-level mma.sync.
 static void gemm(sur_ctx *s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int epi,
                  const float *bias, const float *gate, float *C32, __nv_bfloat16 *C16, __nv_bfloat16 *C16T)
 {
+    if (s->tc) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_tc_smem(NH));
+            attr = true;
+        }
+        const int Np = (N + 15) & ~15;
+        const int tcols = Np <= 32 ? 32 : (Np <= 64 ? 64 : (Np <= 128 ? 128 : 256));
+        k_gemm_tc<<<(M + TC_M - 1) / TC_M, GT_THREADS, gemm_tc_smem(N), s->st>>>(A, B, M, N, K, epi, bias, gate, C32,
+                                                                                 C16, C16T, tcols, s->d_err);
+        return;
+    }
     dim3 grid((N + 63) / 64, (M + 63) / 64);
     k_gemm<<<grid, 128, 0, s->st>>>(A, B, M, N, K, epi, bias, gate, C32, C16, C16T);
 }

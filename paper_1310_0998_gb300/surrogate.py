@@ -127,7 +127,7 @@ class Surrogate:
         return Y, S
 
     def set_backend(self, tcgen05: bool):
-        """Forward products of prediction (>= 128 rows) on tcgen05 or mma.sync."""
+        """Matrix products (training and prediction) on tcgen05 or mma.sync."""
         check(self._lib.sur_set_backend(self._h, 1 if tcgen05 else 0), "sur_set_backend")
 
     def bench_forward(self, n: int, reps: int = 20) -> float:

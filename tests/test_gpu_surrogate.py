@@ -93,6 +93,26 @@ def test_gradients_match_oracle(sur):
     assert np.all(g[0][:, 4:] == 0) and np.all(g[4][40:] == 0) and np.all(g[5][40:] == 0)
 
 
+@pytest.mark.parametrize("n", [150, 1, 512])
+def test_gradients_tcgen05_equal_mma_sync(sur, n):
+    """The training products run on tcgen05 (default) or on warp-level
+    mma.sync; both accumulate in FP32 from the same BF16 operands, so the loss
+    and every gradient agree to FP32 accumulation-order rounding."""
+    p = _params32(31)
+    sur.set_weights(0, p)
+    sur.set_scaling(*_scaling(32))
+    X = _rows(n, 33)
+    Y = np.random.default_rng(34).standard_normal((n, 40)).astype(np.float32)
+    sur.set_backend(True)
+    lt, gt = sur.gradients(0, X, Y)
+    sur.set_backend(False)
+    lm, gm = sur.gradients(0, X, Y)
+    sur.set_backend(True)
+    assert abs(lt - lm) <= 1e-5 * abs(lm)
+    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), gt, gm):
+        assert _rel(a, b) <= 2e-3, (name, _rel(a, b))
+
+
 def test_single_row_and_full_capacity(sur):
     p = _params32(21)
     sur.set_weights(0, p)
