@@ -228,6 +228,11 @@ int dpd_vorticity(dpd_ctx *ctx, int M, double eps, double *omega);
 int dpd_velocity_correlation(dpd_ctx *ctx, double dr, int nbins, double *g, double *L_int,
                              double *num, int64_t *cnt);
 
+/* Sec. 5.3 agent velocities: mean over agents of |v_COM|, v_COM = (v_head +
+ * v_tail) / 2, of the canonical state (FP64 sum on the device).
+ * Synchronises. */
+int dpd_agent_speed(dpd_ctx *ctx, double *mean_speed);
+
 /* Debug / parity: per-cell bead counts of the canonical state, row-major
  * [n_c][n_c] host; and per-bead interacting-neighbour counts (r < r_c,
  * bonded excluded) in id order, host [N], with the total pair count

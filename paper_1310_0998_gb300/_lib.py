@@ -122,6 +122,7 @@ def _declare(L):
         "dpd_energy_spectrum_noalloc": ([vp, c_int, d, vp], c_int),
         "dpd_vorticity": ([vp, c_int, d, vp], c_int),
         "dpd_velocity_correlation": ([vp, d, c_int, vp, P(d), vp, vp], c_int),
+        "dpd_agent_speed": ([vp, P(d)], c_int),
         "dpd_cell_counts": ([vp, vp], c_int),
         "dpd_pair_counts": ([vp, vp, P(u64)], c_int),
         "dpd_get_info": ([vp, P(DpdInfo)], c_int),

@@ -246,6 +246,20 @@ __global__ void __launch_bounds__(VCF_TILE) k_vcf(const double2 *c, const double
     }
 }
 
+// Sum over agents of |v_COM| with v_COM = (v_head + v_tail) / 2, FP64.
+__global__ void k_agent_speed(const uint4 *__restrict__ xv, int na, double *acc)
+{
+    double s = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < na; k += gridDim.x * blockDim.x) {
+        const uint4 h = xv[2 * k], t = xv[2 * k + 1];
+        const double vx = __dmul_rn(0.5, __dadd_rn((double)__uint_as_float(h.z), (double)__uint_as_float(t.z)));
+        const double vy = __dmul_rn(0.5, __dadd_rn((double)__uint_as_float(h.w), (double)__uint_as_float(t.w)));
+        s += sqrt(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
 // ---- velocity correlation limited to r < r_max = nbins dr ------------------
 // Agents are counting-sorted into a periodic grid of ncv x ncv cells of side
 // L / ncv >= r_max, so every pair inside r_max lies in the same or an
@@ -532,6 +546,24 @@ int dpd_vorticity(dpd_ctx *c, int M, double eps, double *omega)
     CUO(cudaGetLastError());
     CUO(cudaMemcpyAsync(omega, om, 8 * MM, cudaMemcpyDeviceToHost, c->st));
     return dpd_internal_latched(c);
+}
+
+int dpd_agent_speed(dpd_ctx *c, double *mean_speed)
+{
+    if (!c || !mean_speed) return DPD_ERR_INVALID_ARG;
+    if (!c->have_state) return DPD_ERR_STATE;
+    const int na = c->d.n / 2;
+    ObsScratch *s = scratch_of(c, 256);
+    if (!s) return DPD_ERR_OOM;
+    double *acc = (double *)s->buf;
+    CUO(cudaMemsetAsync(acc, 0, 8, c->st));
+    k_agent_speed<<<std::min((na + 255) / 256, 1024), 256, 0, c->st>>>(c->d.C_xv, na, acc);
+    CUO(cudaGetLastError());
+    double h = 0.0;
+    CUO(cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, c->st));
+    const int rc = dpd_internal_latched(c);
+    *mean_speed = h / na;
+    return rc;
 }
 
 int dpd_velocity_correlation(dpd_ctx *c, double dr, int nbins, double *g, double *L_int, double *num,

@@ -1190,8 +1190,6 @@ static int sur_simulate_row(void *stream, const float *x, const sur_protocol *pr
     const int nsh = pr->M / 2, nbins = (int)(pr->L / 2 / pr->dr);
     std::vector<double> E((size_t)pr->n_snap * nsh), g((size_t)pr->n_snap * std::max(nbins, 1)), T(pr->n_snap),
         vc(pr->n_snap);
-    std::vector<float> v((size_t)2 * p.n_beads);
-    int64_t st = 0;
     rc = dpd_init_random(c, seed);
     if (!rc) rc = dpd_step(c, pr->burn);
     for (int s = 0; s < pr->n_snap && !rc; ++s) {
@@ -1199,15 +1197,7 @@ static int sur_simulate_row(void *stream, const float *x, const sur_protocol *pr
         if (!rc) rc = dpd_energy_spectrum(c, pr->M, 0.0, &E[(size_t)s * nsh]);
         if (!rc) rc = dpd_velocity_correlation(c, pr->dr, nbins, &g[(size_t)s * nbins], nullptr, nullptr, nullptr);
         if (!rc) rc = dpd_temperature(c, &T[s]);
-        if (!rc) rc = dpd_get_state(c, nullptr, v.data(), nullptr, &st, DPD_HOST);
-        if (!rc) {
-            double m = 0;
-            for (long long a = 0; a < nd; ++a) {
-                const double ux = 0.5 * ((double)v[4 * a] + v[4 * a + 2]), uy = 0.5 * ((double)v[4 * a + 1] + v[4 * a + 3]);
-                m += std::sqrt(ux * ux + uy * uy);
-            }
-            vc[s] = m / nd;
-        }
+        if (!rc) rc = dpd_agent_speed(c, &vc[s]);
     }
     dpd_destroy(c);
     if (!rc) rc = sur_targets(pr->n_snap, nsh, nbins, pr->dr, E.data(), g.data(), T.data(), vc.data(), out);

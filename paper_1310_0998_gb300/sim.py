@@ -130,6 +130,12 @@ class Sim:
         return g, Li.value, num, cnt
 
     # -------------------------------------------------------------- debug
+    def agent_speed(self) -> float:
+        """Mean over agents of |v_COM| (Sec. 5.3), FP64 on the device."""
+        out = ctypes.c_double()
+        check(self._lib.dpd_agent_speed(self._h, ctypes.byref(out)), "dpd_agent_speed")
+        return out.value
+
     def cell_counts(self):
         nc = self.info().n_cells_side
         out = np.zeros((nc, nc), np.uint32)

@@ -58,16 +58,14 @@ def point_params(phi, gamma, zeta, fp, L=SUR_L, seed=0, replica=0):
 def _snapshot(sim, M, dr, nbins):
     E = sim.energy_spectrum(M)
     g, _, _, _ = sim.velocity_correlation(dr, nbins)
-    T = sim.temperature()
-    _, v, _, _ = sim.get_state()
-    vc = 0.5 * (v[0::2].astype(np.float64) + v[1::2])
-    return E, g, T, float(np.mean(np.hypot(vc[:, 0], vc[:, 1])))
+    return E, g, sim.temperature(), sim.agent_speed()
 
 
-def simulate(X, L=SUR_L, burn=2000, n_snap=10, every=200, M=128, dr=0.25, seed=0, batched=True):
+def simulate(X, L=SUR_L, burn=2000, n_snap=10, every=200, M=128, dr=0.25, seed=0, batched=True, chunk=256):
     """Statistics [n][40] of the parameter rows X [n][4] = (phi, gamma, zeta,
-    f_p).  batched: all points as one ensemble (persistent kernel); else one
-    simulation after another (the plain path)."""
+    f_p).  batched: the points as ensembles of up to `chunk` replicas
+    (persistent kernel); else one simulation after another (the plain path).
+    Point i starts from the random initial condition of seed + i."""
     from .ensemble import Ensemble
     from .sim import Sim
     X = np.asarray(X, np.float64)
@@ -75,18 +73,22 @@ def simulate(X, L=SUR_L, burn=2000, n_snap=10, every=200, M=128, dr=0.25, seed=0
     pts = [point_params(*X[i], L=L, seed=seed + i, replica=i) for i in range(X.shape[0])]
     snaps = [[[], [], [], []] for _ in pts]
     if batched:
-        ens = Ensemble(pts)
-        try:
-            ens.init_random(seed)
-            ens.step(burn)
-            for _ in range(n_snap):
-                ens.step(every)
-                ens.sync()
-                for i in range(len(pts)):
-                    for a, b in zip(snaps[i], _snapshot(ens.replica(i), M, dr, nbins)):
-                        a.append(b)
-        finally:
-            ens.close()
+        # replicas in batches of at most `chunk` per persistent launch; replica
+        # i keeps seed + i and replica key i whatever batch it lands in
+        for c0 in range(0, len(pts), chunk):
+            ens = Ensemble(pts[c0:c0 + chunk])
+            try:
+                for r in range(len(pts[c0:c0 + chunk])):
+                    ens.replica(r).init_random(seed + c0 + r)
+                ens.step(burn)
+                for _ in range(n_snap):
+                    ens.step(every)
+                    ens.sync()
+                    for r in range(len(pts[c0:c0 + chunk])):
+                        for a, b in zip(snaps[c0 + r], _snapshot(ens.replica(r), M, dr, nbins)):
+                            a.append(b)
+            finally:
+                ens.close()
     else:
         for i, pt in enumerate(pts):
             kw = {k: v for k, v in pt.items() if k not in ("L", "n_beads")}

@@ -112,3 +112,12 @@ def ensemble_points(R: int, seed: int = 0):
         out.append(dict(L=L, phi=phi, n_dimers=max(1, dimers_for_area_fraction(phi, L)),
                         gamma=gamma, zeta=zeta, fp=fp))
     return out
+
+
+def surrogate_points(n: int, seed: int = 0):
+    """Parameter rows (area fraction, gamma, zeta, f_p) [n][4] drawn from the
+    ranges of the uneven-replica distribution (C4): phi U(0.05, 0.6), gamma
+    log-U(0.5, 50), zeta log-U(0.005, 2), f_p U(0.5, 2)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.05, 0.6, n), np.exp(rng.uniform(math.log(0.5), math.log(50.0), n)),
+                     np.exp(rng.uniform(math.log(0.005), math.log(2.0), n)), rng.uniform(0.5, 2.0, n)], axis=1)

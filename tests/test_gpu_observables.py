@@ -135,3 +135,15 @@ def test_velocity_correlation_full_size(Sim):
     np.testing.assert_allclose(num[:8], np.bincount(bins, weights=dots, minlength=8)[:8], rtol=1e-9,
                                atol=1e-9 * np.abs(dots).sum())
     assert np.all(cnt > 0) and np.isfinite(Li)
+
+
+def test_agent_speed(Sim):
+    """Mean |v_COM| of the agents against its definition in FP64."""
+    L, nd = 37.0, 700
+    x, v = _state(L, nd, 6)
+    with Sim(L, 2 * nd) as s:
+        s.set_positions(x, v)
+        m = s.agent_speed()
+        _, vg, _, _ = s.get_state()
+    vc = 0.5 * (vg[0::2].astype(np.float64) + vg[1::2].astype(np.float64))
+    assert abs(m - float(np.mean(np.hypot(vc[:, 0], vc[:, 1])))) <= 1e-12 * m

@@ -230,14 +230,12 @@ def test_query_falls_back_to_simulation():
 
 
 def _close_stats(a, b):
-    """Two runs of the same point agree up to the run-to-run rounding noise
-    of the force sums (the order of beads within a cell comes from atomics);
-    the peak wavenumber (an argmax) is compared separately."""
+    """Two runs of the same point follow the same trajectory bit for bit (the
+    step is deterministic), so their statistics differ only by the summation
+    order of the FP64 reductions inside the observables, and by the FP32
+    rounding of the query's output."""
     a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
-    keep = np.ones(a.shape[-1], bool)
-    keep[37] = False
-    np.testing.assert_allclose(a[..., keep], b[..., keep], rtol=2e-2, atol=2e-2)
-    assert np.all((a[..., 37] >= 1) & (a[..., 37] <= 64))
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6)
 
 
 def test_statistics_batched_equals_sequential():
@@ -250,3 +248,32 @@ def test_statistics_batched_equals_sequential():
     b = simulate(X, batched=False, **kw)
     assert np.all(np.isfinite(a))
     _close_stats(a, b)
+
+
+def test_network_beats_baselines_on_simulator_statistics():
+    """Trained on statistics this simulator generates (batched ensemble, short
+    runs at L = 32), the network predicts held-out points (plain simulations)
+    better than the two predictors that use no model: the training mean, and
+    the statistics of the nearest training point in standardised inputs."""
+    from paper_1310_0998_gb300 import synth
+    from paper_1310_0998_gb300.surrogate import Surrogate, simulate
+    kw = dict(L=32.0, burn=600, n_snap=4, every=100)
+    X = synth.surrogate_points(320, seed=61).astype(np.float32)
+    Xtr, Xte = X[:256], X[256:]
+    Ytr = simulate(Xtr, batched=True, seed=0, **kw)
+    Yte = simulate(Xte, batched=False, seed=1000, **kw)
+    s = Surrogate(members=4, max_rows=1024, seed=9)
+    try:
+        s.fit(Xtr, Ytr, epochs=300, batch=32, lr=2e-3)
+        P, _ = s.predict(Xte)
+    finally:
+        s.close()
+    sd = Ytr.std(axis=0) + 1e-12
+    cols = [c for c in range(40) if c != 37]          # the argmax k is integer-valued
+    rms = lambda A: float(np.sqrt(np.mean(((A - Yte) / sd)[:, cols] ** 2)))
+    z = lambda A: (np.stack([A[:, 0], np.log(A[:, 1]), np.log(A[:, 2]), A[:, 3]], 1))
+    ztr, zte = z(Xtr.astype(np.float64)), z(Xte.astype(np.float64))
+    mu, sz = ztr.mean(0), ztr.std(0)
+    nn = np.argmin((((zte[:, None, :] - ztr[None, :, :]) / sz) ** 2).sum(-1), axis=1)
+    e_net, e_mean, e_nn = rms(P), rms(np.broadcast_to(Ytr.mean(0), Yte.shape)), rms(Ytr[nn])
+    assert e_net < 0.7 * e_mean and e_net < e_nn, (e_net, e_mean, e_nn)
