@@ -227,6 +227,7 @@ def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0, seq_steps=500):
     for v in views:
         v.sync()
     t_seq = (time.perf_counter() - t0) * steps / seq_steps
+    phases = ens.profile(32)
     info = ens.info()
     shape = views[0].info()
     ens.close()
@@ -235,6 +236,7 @@ def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0, seq_steps=500):
            "sequential_steps_timed": seq_steps, "speedup": t_seq / t_batch,
            "batched_particle_steps_per_s": beads * steps / t_batch, "grid": info["grid"],
            "work_tiles": info["work_tiles"], "tile": shape.tile, "variant": shape.variant,
+           "phases_ms_per_step": phases,
            "timing": "wall clock around each synchronised leg; batched: the full step count in one persistent "
                      "launch per call; sequential: each replica alone, one after another, for "
                      f"{seq_steps} steps, scaled to {steps}"}

@@ -294,6 +294,15 @@ int dpd_batch_barrier_selftest(dpd_batch *b);
 /* Replica count, blocks of the persistent launch, (replica, cell block) items. */
 int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles);
 
+/* Profile of the persistent kernel (no counterpart in the paper): runs
+ * nsteps (1..64) ordinary steps of every replica (they advance, as with
+ * dpd_batch_step) with the kernel's phase log on.  out[0..2]: mean ms per step
+ * of the scan, scatter and force/integrate phases between grid-barrier
+ * releases; out[3..5]: the mean over blocks of the ms a block spent working in
+ * that phase (the difference is time spent waiting at the barrier).
+ * Allocates a small log buffer.  Synchronises. */
+int dpd_batch_profile(dpd_batch *b, int nsteps, double out[6]);
+
 /* Kernel-shape autotuner (no counterpart in the paper: its runs used a CPU
  * molecular-dynamics code).  The cell-block side B in {4, 8, 16} and the pair
  * walk variant (1-5) only change how the step's work is cut into CTAs and

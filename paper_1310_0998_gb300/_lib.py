@@ -136,6 +136,7 @@ def _declare(L):
         "dpd_batch_sync": ([vp], c_int),
         "dpd_batch_barrier_selftest": ([vp], c_int),
         "dpd_batch_info": ([vp, P(c_int), P(c_int), P(c_int)], c_int),
+        "dpd_batch_profile": ([vp, c_int, vp], c_int),
         "dpd_autotune": ([P(DpdParams), vp, vp, c_int, c_int, vp, P(DpdTuneReport)], c_int),
         "dpd_batch_autotune": ([vp, c_int, c_int, vp, P(DpdTuneReport)], c_int),
         "dpd_tune_store": ([P(DpdParams), c_int, c_int, c_int], c_int),

@@ -6,14 +6,15 @@
 // dpd_batch_replica.  The batch adds a device table of the replicas' Sys
 // descriptors, two work lists and one kernel that runs n whole steps for all
 // replicas: per step three phases (cell scan, scatter, fused force/integrate)
-// separated by grid-wide barriers.  Block b takes work items b, b + G,
-// b + 2G, ... (G blocks) of each phase's list (a 4096-cell chunk of a
-// replica's decoupled look-back scan, a 1024-bead chunk to scatter, a
-// (replica, cell block) to integrate); the host
-// shuffles the lists once with a fixed seed so that uneven replicas spread
-// evenly over the blocks.  (Items handed out by atomic counters that block 0
-// reset between phases were measured to process some cell blocks twice; the
-// fixed interleave needs no shared counter.)  The kernel is
+// separated by grid-wide barriers.  In the scan and scatter phases block b
+// takes work items b, b + G, b + 2G, ... (G blocks) of the phase's list (a
+// 4096-cell chunk of a replica's decoupled look-back scan, a 1024-bead chunk
+// to scatter); the host shuffles the scatter list once with a fixed seed so
+// that uneven replicas spread evenly over the blocks.  The force phase's items
+// (replica, cell block) are ordered by estimated cost, largest first, and
+// handed out by a counter that is cleared before each launch and never reset
+// inside it (every block's last, failing take of a step keeps the count per
+// step fixed), which balances the uneven tiles across blocks.  The kernel is
 // launched with no more blocks than can be resident at once and every
 // barrier wait is bounded: a block that gives up latches DPD_ERR_TIMEOUT in
 // the batch's error word instead of hanging.  The launch for a given step
@@ -65,15 +66,33 @@ __device__ void grid_barrier(unsigned *bar, unsigned nblocks, int *err, int skip
     __syncthreads();
 }
 
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Optional phase log (tlog != NULL, a profiling launch): per step s and phase
+// p (scan, scatter, force), block b writes the nanoseconds from the start of
+// the phase to its arrival at the barrier into tlog[(3 s + p) gridDim + b],
+// and block 0 writes the global timer at each barrier release into
+// tlog[3 nsteps gridDim + 4 s + i] (i = 0 at the step's start).
 template <int B, int VAR>
 __global__ void __launch_bounds__(TILE_THREADS, 8)
     k_ensemble(const Sys *__restrict__ sys, const uint32_t *__restrict__ scan_items, int n_scan,
                const uint32_t *__restrict__ scat, int n_scat, const uint32_t *__restrict__ tiles, int n_tiles,
-               unsigned *bar, int *berr, int nsteps, int final_last)
+               unsigned *bar, int *berr, int nsteps, int final_last, unsigned long long *ctr,
+               unsigned long long *tlog)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_item;
     const unsigned nb = gridDim.x;
+    const bool lg = tlog != nullptr && threadIdx.x == 0;
+    unsigned long long *rel = tlog ? tlog + 3ull * nsteps * nb : nullptr;
+    unsigned long long t0 = 0;
     for (int s = 0; s < nsteps; ++s) {
+        if (lg) { t0 = gtimer(); if (blockIdx.x == 0) rel[4 * s] = t0; }
         // phase 1: cell scans; a replica of n cells contributes
         // ceil(n / SCAN_TILE) items, each one chunk of its decoupled
         // look-back scan (the chunk comes from the replica's ticket)
@@ -81,7 +100,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
             const Sys &d = sys[scan_items[it]];
             scan_decoupled_t<TILE_THREADS>(d, (d.ncells + SCAN_TILE - 1) / SCAN_TILE, (uint32_t *)smem);
         }
+        if (lg) tlog[(3ull * s + 0) * nb + blockIdx.x] = gtimer() - t0;
         grid_barrier(bar, nb, berr, 0);
+        if (lg) { t0 = gtimer(); if (blockIdx.x == 0) rel[4 * s + 1] = t0; }
         // phase 2: scatter U -> S in chunks of ENS_CHUNK beads
         for (int it = blockIdx.x; it < n_scat; it += nb) {
             const uint32_t w = scat[it];
@@ -89,10 +110,23 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
             const int k0 = (int)(w & 0x3fffffu) * ENS_CHUNK, k1 = min(d.n, k0 + ENS_CHUNK);
             for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) scatter_one<B>(d, k);
         }
+        if (lg) tlog[(3ull * s + 1) * nb + blockIdx.x] = gtimer() - t0;
         grid_barrier(bar, nb, berr, 0);
-        // phase 3: fused force / integrate / re-bin per (replica, cell block)
+        if (lg) { t0 = gtimer(); if (blockIdx.x == 0) rel[4 * s + 2] = t0; }
+        // phase 3: fused force / integrate / re-bin per (replica, cell block),
+        // the blocks taking items from a counter (the list is ordered by
+        // estimated cost, largest first).  The counter is cleared before the
+        // launch and never reset inside it: in step s every block takes items
+        // until one lies past the list, so the step consumes exactly
+        // n_tiles + gridDim.x values and step s starts at s (n_tiles + gridDim.x).
         const int flags = F_ADVANCE | ((final_last && s == nsteps - 1) ? F_FINAL : 0);
-        for (int it = blockIdx.x; it < n_tiles; it += nb) {
+        const unsigned long long base = (unsigned long long)s * (unsigned long long)(n_tiles + nb);
+        while (true) {
+            if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1ull) - base;
+            __syncthreads();
+            const unsigned long long it = s_item;
+            __syncthreads();
+            if (it >= (unsigned long long)n_tiles) break;
             const uint32_t w = tiles[it];
             const Sys &d = sys[w >> 22];
             Thermo3 th{0.0, 0.0, 0.0};
@@ -101,7 +135,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
             thermo_flush(d, th, (double *)(smem + tile_red_off<B, VAR>()));
             __syncthreads();
         }
+        if (lg) tlog[(3ull * s + 2) * nb + blockIdx.x] = gtimer() - t0;
         grid_barrier(bar, nb, berr, 0);
+        if (lg && blockIdx.x == 0) rel[4 * s + 3] = gtimer();
     }
 }
 
@@ -126,6 +162,7 @@ struct dpd_batch {
     uint32_t *d_scan = nullptr, *d_scat = nullptr, *d_tiles = nullptr;
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
+    unsigned long long *d_ctr = nullptr;   // work counter of the force phase
     int n_scan = 0, n_scat = 0, n_tiles = 0, B = 8, var = 2, cap = 0, grid = 0;
     size_t smem = 0;
     cudaGraphExec_t g = nullptr;
@@ -158,11 +195,11 @@ static int ens_prepare(dpd_batch *b)
 }
 
 template <int B, int VAR>
-static void ens_launch(dpd_batch *b, int nsteps, int final_last)
+static void ens_launch(dpd_batch *b, int nsteps, int final_last, unsigned long long *tlog)
 {
     k_ensemble<B, VAR><<<b->grid, TILE_THREADS, b->smem, b->st>>>(b->d_sys, b->d_scan, b->n_scan, b->d_scat, b->n_scat,
                                                                   b->d_tiles, b->n_tiles, b->d_bar, b->d_err, nsteps,
-                                                                  final_last);
+                                                                  final_last, b->d_ctr, tlog);
 }
 
 static int ens_dispatch_prepare(dpd_batch *b)
@@ -174,28 +211,28 @@ static int ens_dispatch_prepare(dpd_batch *b)
     return b->B == 4 ? ens_prepare<4, 2>(b) : b->B == 8 ? ens_prepare<8, 2>(b) : ens_prepare<16, 2>(b);
 }
 
-static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last)
+static void ens_dispatch_launch(dpd_batch *b, int nsteps, int final_last, unsigned long long *tlog = nullptr)
 {
     if (b->var == 1) {
-        if (b->B == 4) ens_launch<4, 1>(b, nsteps, final_last);
-        else if (b->B == 8) ens_launch<8, 1>(b, nsteps, final_last);
-        else ens_launch<16, 1>(b, nsteps, final_last);
+        if (b->B == 4) ens_launch<4, 1>(b, nsteps, final_last, tlog);
+        else if (b->B == 8) ens_launch<8, 1>(b, nsteps, final_last, tlog);
+        else ens_launch<16, 1>(b, nsteps, final_last, tlog);
     } else if (b->var == 3) {
-        if (b->B == 4) ens_launch<4, 3>(b, nsteps, final_last);
-        else if (b->B == 8) ens_launch<8, 3>(b, nsteps, final_last);
-        else ens_launch<16, 3>(b, nsteps, final_last);
+        if (b->B == 4) ens_launch<4, 3>(b, nsteps, final_last, tlog);
+        else if (b->B == 8) ens_launch<8, 3>(b, nsteps, final_last, tlog);
+        else ens_launch<16, 3>(b, nsteps, final_last, tlog);
     } else if (b->var == 4) {
-        if (b->B == 4) ens_launch<4, 4>(b, nsteps, final_last);
-        else if (b->B == 8) ens_launch<8, 4>(b, nsteps, final_last);
-        else ens_launch<16, 4>(b, nsteps, final_last);
+        if (b->B == 4) ens_launch<4, 4>(b, nsteps, final_last, tlog);
+        else if (b->B == 8) ens_launch<8, 4>(b, nsteps, final_last, tlog);
+        else ens_launch<16, 4>(b, nsteps, final_last, tlog);
     } else if (b->var == 5) {
-        if (b->B == 4) ens_launch<4, 5>(b, nsteps, final_last);
-        else if (b->B == 8) ens_launch<8, 5>(b, nsteps, final_last);
-        else ens_launch<16, 5>(b, nsteps, final_last);
+        if (b->B == 4) ens_launch<4, 5>(b, nsteps, final_last, tlog);
+        else if (b->B == 8) ens_launch<8, 5>(b, nsteps, final_last, tlog);
+        else ens_launch<16, 5>(b, nsteps, final_last, tlog);
     } else {
-        if (b->B == 4) ens_launch<4, 2>(b, nsteps, final_last);
-        else if (b->B == 8) ens_launch<8, 2>(b, nsteps, final_last);
-        else ens_launch<16, 2>(b, nsteps, final_last);
+        if (b->B == 4) ens_launch<4, 2>(b, nsteps, final_last, tlog);
+        else if (b->B == 8) ens_launch<8, 2>(b, nsteps, final_last, tlog);
+        else ens_launch<16, 2>(b, nsteps, final_last, tlog);
     }
 }
 
@@ -220,7 +257,21 @@ static int ens_build_tables(dpd_batch *b)
         for (size_t i = v.size(); i > 1; --i) std::swap(v[i - 1], v[rnd() % i]);
     };
     shuffle(scat);
-    shuffle(tiles);
+    // force items by estimated cost, largest first: pairs per cell grow as the
+    // square of the bead density, times the cells of the block
+    {
+        std::vector<std::pair<double, uint32_t>> cost(tiles.size());
+        for (size_t i = 0; i < tiles.size(); ++i) {
+            const uint32_t w = tiles[i];
+            const Sys &d = sys[w >> 22];
+            const int t = (int)(w & 0x3fffffu), ty = t / d.ntx, tx = t - ty * d.ntx;
+            const int tw = std::min(b->B, d.nc - tx * b->B), th = std::min(b->B, d.nc - ty * b->B);
+            const double rho = (double)d.n / ((double)d.L * d.L);
+            cost[i] = {-(rho * rho * tw * th), w};
+        }
+        std::stable_sort(cost.begin(), cost.end());
+        for (size_t i = 0; i < tiles.size(); ++i) tiles[i] = cost[i].second;
+    }
     for (int r = 0; r < b->R; ++r) order[r] = (uint32_t)r;
     std::stable_sort(order.begin(), order.end(), [&sys](uint32_t a, uint32_t c) { return sys[a].ncells > sys[c].ncells; });
     for (uint32_t r : order)
@@ -244,6 +295,7 @@ static int ens_build_tables(dpd_batch *b)
     b->d_tiles = (uint32_t *)p; p += (4 * tiles.size() + 255) & ~size_t(255);
     b->d_bar = (unsigned *)p;          // 2 words
     b->d_err = (int *)(b->d_bar + 8);  // 1 word
+    b->d_ctr = (unsigned long long *)(b->d_bar + 16);
     CUB(cudaMemcpyAsync(b->d_sys, sys.data(), sizeof(Sys) * (size_t)b->R, cudaMemcpyHostToDevice, b->st));
     CUB(cudaMemcpyAsync(b->d_scan, scan.data(), 4 * scan.size(), cudaMemcpyHostToDevice, b->st));
     CUB(cudaMemcpyAsync(b->d_scat, scat.data(), 4 * scat.size(), cudaMemcpyHostToDevice, b->st));
@@ -352,6 +404,7 @@ int dpd_batch_step(dpd_batch *b, int64_t n)
         b->g = nullptr;
         cudaGraph_t gr = nullptr;
         CUB(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long), b->st);
         ens_dispatch_launch(b, (int)n, 1);
         const cudaError_t e = cudaStreamEndCapture(b->st, &gr);
         if (e != cudaSuccess) return DPD_ERR_CUDA;
@@ -398,6 +451,44 @@ int dpd_batch_barrier_selftest(dpd_batch *b)
     CUB(cudaMemsetAsync(b->d_bar, 0, 64, b->st));
     CUB(cudaStreamSynchronize(b->st));
     return (seen & ERR_TIMEOUT) ? DPD_ERR_TIMEOUT : DPD_OK;
+}
+
+int dpd_batch_profile(dpd_batch *b, int nsteps, double out[6])
+{
+    if (!b || !out || nsteps < 1 || nsteps > 64) return DPD_ERR_INVALID_ARG;
+    for (dpd_ctx *c : b->reps)
+        if (!c->have_state) return DPD_ERR_STATE;
+    const size_t n_blk = 3ull * nsteps * (size_t)b->grid, n_rel = 4ull * nsteps;
+    unsigned long long *dlog = nullptr;
+    CUB(cudaMalloc(&dlog, 8 * (n_blk + n_rel)));
+    CUB(cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long), b->st));
+    ens_dispatch_launch(b, nsteps, 1, dlog);
+    std::vector<unsigned long long> h(n_blk + n_rel);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dlog, 8 * h.size(), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    cudaFree(dlog);
+    if (e != cudaSuccess) return DPD_ERR_CUDA;
+    for (dpd_ctx *c : b->reps) {
+        c->step += nsteps;
+        c->sorted_canonical = true;
+    }
+    // phase durations between barrier releases, and the mean over blocks of
+    // the time a block worked in the phase (the rest is waiting at the barrier)
+    double dur[3] = {0, 0, 0}, busy[3] = {0, 0, 0};
+    const unsigned long long *rel = h.data() + n_blk;
+    for (int s = 0; s < nsteps; ++s)
+        for (int p = 0; p < 3; ++p) {
+            dur[p] += (double)(rel[4 * s + p + 1] - rel[4 * s + p]);
+            double sum = 0;
+            for (int blk = 0; blk < b->grid; ++blk) sum += (double)h[(3ull * s + p) * b->grid + blk];
+            busy[p] += sum / b->grid;
+        }
+    for (int p = 0; p < 3; ++p) {
+        out[p] = dur[p] / nsteps / 1e6;
+        out[3 + p] = busy[p] / nsteps / 1e6;
+    }
+    return dpd_batch_sync(b);
 }
 
 int dpd_batch_info(dpd_batch *b, int *n_replicas, int *grid, int *n_work_tiles)

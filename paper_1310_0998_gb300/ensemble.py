@@ -53,6 +53,16 @@ class Ensemble:
     def barrier_selftest(self) -> int:
         return int(self._lib.dpd_batch_barrier_selftest(self._h))
 
+    def profile(self, nsteps: int = 16):
+        """Run nsteps steps with the phase log on: per-step ms of the scan,
+        scatter and force phases (barrier to barrier) and the mean ms a block
+        worked in each."""
+        import numpy as np
+        out = np.zeros(6, np.float64)
+        check(self._lib.dpd_batch_profile(self._h, int(nsteps), _lib.ptr(out)), "dpd_batch_profile")
+        return {"scan_ms": out[0], "scatter_ms": out[1], "force_ms": out[2],
+                "scan_busy_ms": out[3], "scatter_busy_ms": out[4], "force_busy_ms": out[5]}
+
     def info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(self._lib.dpd_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "dpd_batch_info")

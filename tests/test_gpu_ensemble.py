@@ -139,3 +139,27 @@ def test_replica_views_are_borrowed(mods):
         ens.step(3)
         ens.sync()
         assert view.get_state()[3] == 3
+
+
+def test_profile_runs_the_same_steps(mods):
+    """The phase-logged launch advances the replicas exactly as an ordinary
+    step call does, and reports positive phase times with the busy time of a
+    block inside its phase."""
+    Ensemble, _ = mods
+    pts = _points()[:4]
+    out = []
+    for prof in (True, False):
+        with Ensemble(pts) as ens:
+            ens.init_random(21)
+            if prof:
+                ph = ens.profile(12)
+            else:
+                ens.step(12)
+                ens.sync()
+            out.append([ens.replica(r).get_state() for r in range(len(pts))])
+    for a, b in zip(out[0], out[1]):
+        assert a[3] == b[3] == 12
+        for u, w in zip(a[:3], b[:3]):
+            np.testing.assert_array_equal(u, w)
+    for k in ("scan", "scatter", "force"):
+        assert ph[k + "_ms"] > 0 and 0 < ph[k + "_busy_ms"] <= ph[k + "_ms"] * 1.05, ph
