@@ -2,7 +2,7 @@
 single-system path does, for replicas of uneven box size, bead count and
 parameters; its grid barrier gives up after a bounded wait.
 
-Pair forces are summed per bead in 64-bit fixed point (order-independent) from
+Pair forces are summed per bead in fixed point (order-independent) from
 pair terms that are exact negations of each other whichever bead or tile
 evaluates them, so a replica's trajectory is the same bits in the batch and
 alone, whatever the cell order the atomic binning produced.  Only the FP64

@@ -370,7 +370,7 @@ def test_trajectory_bit_identical_across_kernel_shapes(Sim):
     """Every pair variant and tile size produces the same trajectory bits: the
     pair term is an exact function of the two beads (exact fixed-point
     separation, Philox keyed on the unordered pair), opposite from the two
-    sides, and a bead's pair forces are summed in 64-bit fixed point, so
+    sides, and a bead's pair forces are summed in fixed point, so
     neither the staging order, the Newton-3 side nor the atomic cell order
     changes a bit.  A clustered quarter makes some tiles take the
     global-memory path in some shapes; that path gives the same bits too."""
