@@ -245,6 +245,91 @@ def ensemble_leg(R, steps, warmup, seed=0, variant=0, tile=0, seq_steps=500):
     return out
 
 
+def sweep_leg(steps=20000, snaps=5, every=2000, M=128, seq_steps=2000, seed=0, sur=None):
+    """C2: the parameter sweep of the 256 x 256 box (area fraction 0.1-0.6 x
+    gamma {1, 4.5, 20} x zeta {0.01, 0.1, 1}, 54 points, f_p = 1), each point
+    `steps` steps from the paper's initial condition with the FP64 E(k) on
+    M^2 averaged over `snaps` snapshots `every` steps apart at the end of the
+    run.  Batched: all points in the persistent ensemble kernel (shape tuned
+    for the mix).  Plain: every point alone through the single-system path,
+    one after another (context creation, initial state, `seq_steps` steps
+    scaled to `steps`, and all its snapshots, timed).  With a trained
+    surrogate, the time it takes to answer the same 54 points (fallback rule
+    included) is reported beside them."""
+    import torch
+    from paper_1310_0998_gb300 import Ensemble, Sim, synth, tune
+    pts = []
+    for r, e in enumerate(synth.sweep_points()):
+        pts.append(dict(a=PHYS["a"], kBT=PHYS["kBT"], rc=PHYS["rc"], k_bond=PHYS["kbond"], r0=PHYS["r0"],
+                        dt=PHYS["dt"], L=e["L"], n_beads=2 * e["n_dimers"], gamma=e["gamma"], zeta=e["zeta"],
+                        f_p=e["fp"], seed=seed + r, replica=r))
+    R = len(pts)
+    beads = sum(p["n_beads"] for p in pts)
+    every = max(1, min(every, steps // snaps))
+    burn = max(0, steps - snaps * every)
+    seq_steps = max(1, min(seq_steps, steps))
+    tuning = tune.batch_autotune(pts, steps=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens = Ensemble(pts)
+    ens.init_random(seed)
+    ens.sync()
+    t_setup = time.perf_counter() - t0
+    E = np.zeros((R, M // 2))
+    t0 = time.perf_counter()
+    for k in range(snaps + 1):
+        n = burn if k == 0 else every
+        while n > 0:
+            c = min(n, 10000)
+            ens.step(c)
+            ens.sync()
+            n -= c
+        if k > 0:
+            for r in range(R):
+                E[r] += ens.replica(r).energy_spectrum(M) / snaps
+    t_run = time.perf_counter() - t0
+    shape = ens.replica(0).info()
+    ens.close()
+    t_seq = 0.0
+    for r, p in enumerate(pts):
+        kw = dict(p)
+        L, n = kw.pop("L"), kw.pop("n_beads")
+        t0 = time.perf_counter()
+        s = Sim(L, n, **kw)
+        s.init_random(seed)
+        s.sync()
+        t1 = time.perf_counter()
+        s.step(seq_steps)
+        s.sync()
+        t2 = time.perf_counter()
+        for _ in range(snaps):
+            s.energy_spectrum(M)
+        t3 = time.perf_counter()
+        s.close()
+        t_seq += (t1 - t0) + (t2 - t1) * steps / seq_steps + (t3 - t2)
+    out = {"points": R, "beads": beads, "steps": steps, "snapshots": snaps, "every": every, "M": M,
+           "batched_setup_s": t_setup, "batched_run_s": t_run, "batched_s": t_setup + t_run,
+           "batched_particle_steps_per_s": beads * steps / t_run,
+           "plain_s": t_seq, "plain_steps_timed_per_point": seq_steps,
+           "speedup": t_seq / (t_setup + t_run), "tile": shape.tile, "variant": shape.variant,
+           "spectra_finite": bool(np.all(np.isfinite(E)) and np.all(E > 0)), "tuning": tuning,
+           "timing": "wall clock; batched: set-up, then all steps in persistent launches of up to 1e4 steps and "
+                     "the E(k) of every point at each snapshot; plain: per point set-up, seq_steps steps scaled "
+                     "to the full count, and every snapshot's E(k)"}
+    if sur is not None:
+        Xq = np.array([[synth.sweep_points()[r]["phi"], p["gamma"], p["zeta"], p["f_p"]]
+                       for r, p in enumerate(pts)], np.float32)
+        model, thr, proto = sur
+        t0 = time.perf_counter()
+        _, fb = model.query(Xq, thr, dict(proto, seed=seed))
+        t_q = time.perf_counter() - t0
+        out.update({"surrogate_s": t_q, "surrogate_fallback_points": int(fb.sum()),
+                    "surrogate_speedup_vs_plain": t_seq / t_q,
+                    "surrogate_note": "the surrogate answers its own sampling protocol's statistics (L = 48 box) "
+                                      "at the sweep's parameters; its accuracy is the surrogate leg's"})
+    return out
+
+
 def observables_leg(sim, nb, reps=5):
     """Observables on the device (Secs. 5.3-5.4): E(k) at M = 128 on the main
     box's state (agent centres of mass, windowed velocity field, the library's
@@ -301,16 +386,23 @@ def three_d_leg(steps=20, warmup=3, L=64.0, seed=0):
         s.step(steps)
         s.sync()
         dt = time.perf_counter() - t0
+        s.energy_spectrum(64)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            s.energy_spectrum(64)
+        spec_ms = (time.perf_counter() - t0) / 3 * 1e3
     rate = nb * steps / dt
     pk = peaks()
     alu_peak = sm_count() * LANES * pk["sm_max_mhz"] * 1e6
     return {"beads": nb, "L": L, "steps": steps, "particle_steps_per_s": rate, "ms_per_step": 1e3 * dt / steps,
             "roofline": {"bound": "alu", "achieved": OPS_PER_BEAD_STEP_3D * rate / 1e12, "peak": alu_peak / 1e12,
                          "unit": "Tops/s", "frac": OPS_PER_BEAD_STEP_3D * rate / alu_peak},
-            "timing": "wall clock around synchronised steps (scan, scatter, pair forces, integration per step)"}
+            "spectrum_M": 64, "spectrum_ms": spec_ms,
+            "timing": "wall clock around synchronised steps (scan, scatter, pair forces, integration per step); "
+                      "spectrum: per synchronising call (COM, windowed field on 64^3, FFT, shells)"}
 
 
-def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0):
+def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0, keep=False):
     """C5: the learned surrogate of the simulator's statistics.  Parameter
     points (area fraction, gamma, zeta, f_p) from the C4 ranges; the training
     statistics come from batched-ensemble runs (chunks of 256 replicas), the
@@ -322,7 +414,9 @@ def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0):
     two model-free predictors (training mean, nearest training point), the
     run-to-run noise floor of the statistics (a second plain run of the first
     n_noise held-out points with other seeds), the fallback rate, the query
-    speedup, and the device throughput of the tensor-core forward pass."""
+    speedup, and the device throughput of the tensor-core forward pass.
+    keep: also return the trained model, its fallback threshold and protocol
+    (the caller closes the model)."""
     import numpy as np
     from paper_1310_0998_gb300 import surrogate as S, synth
     proto = dict(L=48.0, burn=1500, n_snap=6, every=250)
@@ -338,6 +432,7 @@ def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0):
     ok_tr = np.all(np.isfinite(Ytr), axis=1)
     ok_te = np.all(np.isfinite(Yte), axis=1)
     sur = S.Surrogate(members=4, max_rows=4096, seed=seed)
+    trained = False
     try:
         t0 = time.perf_counter()
         loss = sur.fit(Xtr[ok_tr], Ytr[ok_tr], epochs=300, batch=64, lr=2e-3)
@@ -355,8 +450,10 @@ def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0):
         for _ in range(reps):
             sur.predict(Xb)
         t_pred = (time.perf_counter() - t0) / reps
+        trained = True
     finally:
-        sur.close()
+        if not (keep and trained):
+            sur.close()
 
     def errors(A, B):
         """median over points of the mean E(k) error, and of the xi / L_gv errors"""
@@ -408,7 +505,7 @@ def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0):
                              "unit": "TFLOP/s", "frac": tc_tflops / peak, "peak_src": "measured bf16 burst"},
                 "note": "errors: medians over held-out points; E_k error is the mean over the 32 shell-pair bins "
                         "of |E_pred/E_sim - 1|; predict_rows_per_s: 4096-row C-ABI calls with host copies"})
-    return out
+    return (out, (sur, thr, proto)) if keep else out
 
 
 def run_reference(args, cfg):
@@ -462,6 +559,9 @@ def main():
     ap.add_argument("--ens-replicas", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=10000)
     ap.add_argument("--ens-seq-steps", type=int, default=500)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the C2 parameter-sweep leg")
+    ap.add_argument("--sweep-steps", type=int, default=20000)
+    ap.add_argument("--sweep-seq-steps", type=int, default=2000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = CONFIGS[args.config]
@@ -608,8 +708,14 @@ def main():
     if rank == 0 and not args.no_ensemble:
         line["ensemble"] = ensemble_leg(args.ens_replicas, args.ens_steps, args.warmup, variant=args.variant,
                                         tile=args.tile, seq_steps=min(args.ens_seq_steps, args.ens_steps))
+    model = None
     if rank == 0 and not args.no_surrogate:
-        line["surrogate"] = surrogate_leg()
+        line["surrogate"], model = surrogate_leg(keep=True)
+    if rank == 0 and not args.no_sweep:
+        line["sweep"] = sweep_leg(steps=args.sweep_steps, seq_steps=min(args.sweep_seq_steps, args.sweep_steps),
+                                  sur=model)
+    if model is not None:
+        model[0].close()
     if rank == 0 and not args.no_obs:
         line["observables"] = observables_leg(sim, nb)
     if rank == 0 and not args.no_3d:

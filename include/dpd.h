@@ -360,6 +360,32 @@ int dpd3_get_state(dpd3_ctx *ctx, double *x, float *v, float *f, int64_t *step);
  * T = m sum |v|^2 / (3N - 3); out = (KE, Px, Py, Pz, T).  Synchronises. */
 int dpd3_thermo(dpd3_ctx *ctx, double out[5]);
 
+/* Observables of Secs. 5.3-5.4 carried to the cube, FP64, from the canonical
+ * state of the last call (agent k = beads 2k head, 2k+1 tail; centre of mass
+ * c_k = x_tail + minimg(x_head - x_tail)/2 wrapped, v_k = (v_head + v_tail)/2).
+ * Filter: cubic window of side eps (eps <= 0: L (10 / N_agents)^(1/3), the
+ * window holding 10 agents on average) centred on (i + 1/2) L/M per axis,
+ * closed, minimum image; an empty window gives u = 0; eps / (L / M) > 28 is
+ * DPD_ERR_INVALID_ARG.  Grids are z-major [iz][iy][ix]; host outputs.
+ * Scratch (about 64 M^3 + 64 N_agents bytes) is allocated on first use and
+ * kept with the context.  Synchronise. */
+/* u [M^3][3] = u_M (x, y, z); n_in [M^3] window counts (may be NULL); 2 <= M <= 256. */
+int dpd3_velocity_field(dpd3_ctx *ctx, int M, double eps, double *u, double *n_in);
+/* E [M/2]: E(k), k = 1..M/2, uhat = M^-3 sum u exp(-2 pi i k.x/L) per
+ * component, E(k) = sum over nint|k| = k of (|uhat_x|^2+|uhat_y|^2+|uhat_z|^2)/2;
+ * M a power of two in [4, 256]. */
+int dpd3_energy_spectrum(dpd3_ctx *ctx, int M, double eps, double *E);
+/* omega [M^3][3] = curl u_M by second-order central differences on the
+ * periodic grid of spacing L/M; 3 <= M <= 256. */
+int dpd3_vorticity(dpd3_ctx *ctx, int M, double eps, double *omega);
+/* Velocity correlation over all agent pairs a < b with COM separation
+ * r = sqrt((dx^2 + dy^2) + dz^2) (minimum image) in bin floor(r / dr) <
+ * nbins (1 <= nbins <= 4096): g [nbins] as in dpd_velocity_correlation (NaN
+ * for an empty bin), *L_int by the trapezoid rule, num / cnt the raw sums
+ * and pair counts (may be NULL).  O(N_agents^2) work. */
+int dpd3_velocity_correlation(dpd3_ctx *ctx, double dr, int nbins, double *g, double *L_int, double *num,
+                              int64_t *cnt);
+
 /* ------------------------------------------------------------------------
  * Learned surrogate of ensemble statistics (not part of the paper: a model
  * of this simulator's own outputs).  A deep ensemble of K MLPs

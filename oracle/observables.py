@@ -168,3 +168,104 @@ def velocity_correlation(c, vc, L, dr, nbins):
     num, cnt = vcf_sums(c, vc, L, dr, nbins)
     g = vcf_from_sums(num, cnt, vc)
     return g, integral_length(g, cnt, dr), num, cnt
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions.  The paper defines the observables in two dimensions; the
+# three-dimensional variant carries each over axis by axis (readings):
+#   * cubic window of side eps, |dx|, |dy|, |dz| <= eps/2 (minimum image),
+#     grid points (i + 1/2) L/M per axis, default eps = L (N_f/N)^(1/3) (the
+#     window holds N_f agents on average, as the square window does in 2D);
+#   * uhat = M^-3 sum u exp(-2 pi i k.x/L), E(k) = sum over nint|k| = k of
+#     (|uhat_x|^2 + |uhat_y|^2 + |uhat_z|^2)/2, k = 1..M/2;
+#   * vorticity: the curl of u_M by central differences;
+#   * velocity correlation: all pairs, r = sqrt((dx^2 + dy^2) + dz^2).
+# agent_com, vcf_from_sums and integral_length above work in any dimension.
+# Layouts: grids [iz, iy, ix] (+ component last).
+
+def filter_width3(L, n_agents, n_f=10.0):
+    """eps = L (N_f / N)^(1/3)."""
+    return L * (n_f / n_agents) ** (1.0 / 3.0)
+
+
+def velocity_field3(c, vc, L, M, eps, chunk=8192):
+    """u_M on the M^3 grid, layout [iz, iy, ix, component], and the counts."""
+    c = np.asarray(c, np.float64)
+    vc = np.asarray(vc, np.float64)
+    xm = (np.arange(M) + 0.5) * (L / M)
+    half = 0.5 * eps
+    n = np.zeros((M, M, M))
+    s = np.zeros((3, M, M, M))
+    for a0 in range(0, c.shape[0], chunk):
+        cc, vv = c[a0:a0 + chunk], vc[a0:a0 + chunk]
+        inc = [(np.abs(_minimg(xm[None, :] - cc[:, d:d + 1], L)) <= half).astype(np.float64) for d in range(3)]
+        n += np.einsum("az,ay,ax->zyx", inc[2], inc[1], inc[0])
+        for d in range(3):
+            s[d] += np.einsum("az,ay,ax->zyx", inc[2] * vv[:, d:d + 1], inc[1], inc[0])
+    u = np.zeros((M, M, M, 3), np.float64)
+    nz = n > 0
+    for d in range(3):
+        u[..., d][nz] = s[d][nz] / n[nz]
+    return u, n
+
+
+def fourier3(u):
+    """uhat = M^-3 sum u exp(-2 pi i k.x/L) per component; [kz, ky, kx, comp]."""
+    M = u.shape[0]
+    return np.stack([np.fft.fftn(u[..., d]) for d in range(3)], axis=-1) / float(M) ** 3
+
+
+def shell_index3(M):
+    k = np.fft.fftfreq(M, d=1.0 / M)
+    kk = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    return np.rint(kk).astype(np.int64)
+
+
+def energy_spectrum3(u):
+    """E(k), k = 1..M/2 (index 0 of the result is k = 1)."""
+    M = u.shape[0]
+    uh = fourier3(u)
+    e2 = 0.5 * np.sum(np.abs(uh) ** 2, axis=-1)
+    sh = shell_index3(M)
+    return np.array([e2[sh == k].sum() for k in range(1, M // 2 + 1)], np.float64)
+
+
+def vorticity3(u, L):
+    """curl u of a field u [iz, iy, ix, comp] on the periodic M^3 grid of
+    spacing L / M, second-order central differences; [iz, iy, ix, 3]."""
+    u = np.asarray(u, np.float64)
+    h = L / u.shape[0]
+
+    def d(comp, axis):   # axis 0 = z, 1 = y, 2 = x of the grid
+        return (np.roll(u[..., comp], -1, axis=axis) - np.roll(u[..., comp], 1, axis=axis)) / (2.0 * h)
+
+    return np.stack([d(2, 1) - d(1, 0), d(0, 0) - d(2, 2), d(1, 2) - d(0, 1)], axis=-1)
+
+
+def vcf_sums3(c, vc, L, dr, nbins, chunk=1024):
+    """Pair sums per separation bin in 3D: (sum v_a.v_b, pair count)."""
+    c = np.asarray(c, np.float64)
+    vc = np.asarray(vc, np.float64)
+    n = c.shape[0]
+    num = np.zeros(nbins, np.float64)
+    cnt = np.zeros(nbins, np.int64)
+    for a0 in range(0, n, chunk):
+        a1 = min(n, a0 + chunk)
+        dx = _minimg(c[a0:a1, None, 0] - c[None, :, 0], L)
+        dy = _minimg(c[a0:a1, None, 1] - c[None, :, 1], L)
+        dz = _minimg(c[a0:a1, None, 2] - c[None, :, 2], L)
+        r = np.sqrt(dx * dx + dy * dy + dz * dz)
+        b = np.floor(r / dr)
+        dot = (vc[a0:a1, None, 0] * vc[None, :, 0] + vc[a0:a1, None, 1] * vc[None, :, 1]
+               + vc[a0:a1, None, 2] * vc[None, :, 2])
+        keep = (np.arange(n)[None, :] > np.arange(a0, a1)[:, None]) & (b < nbins)
+        bi = b[keep].astype(np.int64)
+        num += np.bincount(bi, weights=dot[keep], minlength=nbins)
+        cnt += np.bincount(bi, minlength=nbins)
+    return num, cnt
+
+
+def velocity_correlation3(c, vc, L, dr, nbins):
+    num, cnt = vcf_sums3(c, vc, L, dr, nbins)
+    g = vcf_from_sums(num, cnt, vc)
+    return g, integral_length(g, cnt, dr), num, cnt

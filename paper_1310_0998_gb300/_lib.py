@@ -149,6 +149,10 @@ def _declare(L):
         "dpd3_sync": ([vp], c_int),
         "dpd3_get_state": ([vp, vp, vp, vp, P(i64)], c_int),
         "dpd3_thermo": ([vp, vp], c_int),
+        "dpd3_velocity_field": ([vp, c_int, d, vp, vp], c_int),
+        "dpd3_energy_spectrum": ([vp, c_int, d, vp], c_int),
+        "dpd3_vorticity": ([vp, c_int, d, vp], c_int),
+        "dpd3_velocity_correlation": ([vp, d, c_int, vp, P(d), vp, vp], c_int),
         "sur_create": ([c_int, c_int, u64, vp, P(vp)], c_int),
         "sur_destroy": ([vp], None),
         "sur_set_weights": ([vp, c_int, vp, vp, vp, vp, vp, vp], c_int),

@@ -4,17 +4,17 @@
 // Each replica is an ordinary context (its own buffers, cell list, thermo log
 // and canonical state), so every single-system call also works on it through
 // dpd_batch_replica.  The batch adds a device table of the replicas' Sys
-// descriptors, two work lists and one kernel that runs n whole steps for all
+// descriptors, three work lists and one kernel that runs n whole steps for all
 // replicas: per step three phases (cell scan, scatter, fused force/integrate)
-// separated by grid-wide barriers.  In the scan and scatter phases block b
-// takes work items b, b + G, b + 2G, ... (G blocks) of the phase's list (a
-// 4096-cell chunk of a replica's decoupled look-back scan, a 1024-bead chunk
-// to scatter); the host shuffles the scatter list once with a fixed seed so
-// that uneven replicas spread evenly over the blocks.  The force phase's items
-// (replica, cell block) are ordered by estimated cost, largest first, and
-// handed out by a counter that is cleared before each launch and never reset
-// inside it (every block's last, failing take of a step keeps the count per
-// step fixed), which balances the uneven tiles across blocks.  The kernel is
+// separated by grid-wide barriers.  In the scan phase block b takes work
+// items b, b + G, b + 2G, ... (G blocks) of the list of 4096-cell chunks of
+// the replicas' decoupled look-back scans.  The scatter phase's items
+// (1024-bead chunks, shuffled once with a fixed seed so that a replica's
+// chunks spread out) and the force phase's items (replica, cell block),
+// ordered by estimated cost, largest first, are handed out by two counters
+// that are cleared before each launch and never reset inside it (every
+// block's last, failing take of a step keeps the count per step fixed),
+// which balances uneven items across blocks.  The kernel is
 // launched with no more blocks than can be resident at once and every
 // barrier wait is bounded: a block that gives up latches DPD_ERR_TIMEOUT in
 // the batch's error word instead of hanging.  The launch for a given step
@@ -66,6 +66,44 @@ __device__ void grid_barrier(unsigned *bar, unsigned nblocks, int *err, int skip
     __syncthreads();
 }
 
+// Scatter U -> S of the beads [k0, k1) of one replica, four beads per thread
+// in flight (their loads issued before any store), which a latency-bound
+// phase of a few warps per SM needs.  Same result as scatter_one per bead.
+template <int B>
+__device__ __forceinline__ void scatter_chunk(const Sys &d, int k0, int k1)
+{
+    constexpr int U = 4;
+    const int bd = blockDim.x;
+    for (int kb = k0 + (int)threadIdx.x; kb < k1; kb += U * bd) {
+        uint4 xv[U];
+        uint32_t id[U], dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = kb + u * bd;
+            if (k < k1) {
+                xv[u] = d.U_xv[k];
+                id[u] = d.U_id[k];
+                dst[u] = d.U_rank[k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (kb + u * bd < k1) dst[u] += d.cstart[cell_of<B>(d, cell_coord(d, xv[u].x), cell_coord(d, xv[u].y))];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = kb + u * bd;
+            if (k >= k1) continue;
+            if (dst[u] >= (uint32_t)d.n || id[u] >= (uint32_t)d.n) {
+                set_err_at(d, ERR_INTERNAL, 1, k, dst[u], id[u]);
+                continue;
+            }
+            d.S_xv[dst[u]] = xv[u];
+            d.S_id[dst[u]] = id[u];
+            d.slot[id[u]] = dst[u];
+        }
+    }
+}
+
 __device__ __forceinline__ unsigned long long gtimer()
 {
     unsigned long long t;
@@ -103,12 +141,20 @@ __global__ void __launch_bounds__(TILE_THREADS, 8)
         if (lg) tlog[(3ull * s + 0) * nb + blockIdx.x] = gtimer() - t0;
         grid_barrier(bar, nb, berr, 0);
         if (lg) { t0 = gtimer(); if (blockIdx.x == 0) rel[4 * s + 1] = t0; }
-        // phase 2: scatter U -> S in chunks of ENS_CHUNK beads
-        for (int it = blockIdx.x; it < n_scat; it += nb) {
+        // phase 2: scatter U -> S in chunks of ENS_CHUNK beads, the chunks
+        // taken from the second counter (step s starts at s (n_scat + G),
+        // as in the force phase below)
+        const unsigned long long sbase = (unsigned long long)s * (unsigned long long)(n_scat + nb);
+        while (true) {
+            if (threadIdx.x == 0) s_item = atomicAdd(ctr + 1, 1ull) - sbase;
+            __syncthreads();
+            const unsigned long long it = s_item;
+            __syncthreads();
+            if (it >= (unsigned long long)n_scat) break;
             const uint32_t w = scat[it];
             const Sys &d = sys[w >> 22];
-            const int k0 = (int)(w & 0x3fffffu) * ENS_CHUNK, k1 = min(d.n, k0 + ENS_CHUNK);
-            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) scatter_one<B>(d, k);
+            const int k0 = (int)(w & 0x3fffffu) * ENS_CHUNK;
+            scatter_chunk<B>(d, k0, min(d.n, k0 + ENS_CHUNK));
         }
         if (lg) tlog[(3ull * s + 1) * nb + blockIdx.x] = gtimer() - t0;
         grid_barrier(bar, nb, berr, 0);
@@ -162,7 +208,7 @@ struct dpd_batch {
     uint32_t *d_scan = nullptr, *d_scat = nullptr, *d_tiles = nullptr;
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
-    unsigned long long *d_ctr = nullptr;   // work counter of the force phase
+    unsigned long long *d_ctr = nullptr;   // work counters: [0] force phase, [1] scatter phase
     int n_scan = 0, n_scat = 0, n_tiles = 0, B = 8, var = 2, cap = 0, grid = 0;
     size_t smem = 0;
     cudaGraphExec_t g = nullptr;
@@ -404,7 +450,7 @@ int dpd_batch_step(dpd_batch *b, int64_t n)
         b->g = nullptr;
         cudaGraph_t gr = nullptr;
         CUB(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-        cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long), b->st);
+        cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(unsigned long long), b->st);
         ens_dispatch_launch(b, (int)n, 1);
         const cudaError_t e = cudaStreamEndCapture(b->st, &gr);
         if (e != cudaSuccess) return DPD_ERR_CUDA;
@@ -461,7 +507,7 @@ int dpd_batch_profile(dpd_batch *b, int nsteps, double out[6])
     const size_t n_blk = 3ull * nsteps * (size_t)b->grid, n_rel = 4ull * nsteps;
     unsigned long long *dlog = nullptr;
     CUB(cudaMalloc(&dlog, 8 * (n_blk + n_rel)));
-    CUB(cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long), b->st));
+    CUB(cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(unsigned long long), b->st));
     ens_dispatch_launch(b, nsteps, 1, dlog);
     std::vector<unsigned long long> h(n_blk + n_rel);
     cudaError_t e = cudaGetLastError();

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "dpd.h"
+#include "obs_common.cuh"
 #include "sim_host.h"
 
 namespace dpd {
@@ -28,11 +29,6 @@ struct ObsScratch {
     void *buf = nullptr;
     size_t bytes = 0;
 };
-
-__device__ __forceinline__ double minimg_d(double d, double L)
-{
-    return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
-}
 
 // Positions enter as the exact doubles X L / 2^32 of the fixed-point state.
 __global__ void k_agent_com(const uint4 *__restrict__ xv, int na, double L, double ulen, double2 *c, double2 *v)
@@ -52,23 +48,6 @@ __global__ void k_agent_com(const uint4 *__restrict__ xv, int na, double L, doub
     const double hvx = (double)__uint_as_float(h.z), hvy = (double)__uint_as_float(h.w);
     const double tvx = (double)__uint_as_float(t.z), tvy = (double)__uint_as_float(t.w);
     v[k] = make_double2(__dmul_rn(0.5, __dadd_rn(hvx, tvx)), __dmul_rn(0.5, __dadd_rn(hvy, tvy)));
-}
-
-// Grid indices i whose window [x_i - eps/2, x_i + eps/2] (minimum image)
-// contains coordinate c; at most M of them.
-__device__ __forceinline__ int window_hits(double c, double L, double dxg, double half, int M, int *out, int maxout)
-{
-    const double lo = (c - half) / dxg - 0.5, hi = (c + half) / dxg - 0.5;
-    int i0 = (int)floor(lo) - 1, i1 = (int)ceil(hi) + 1;
-    if (i1 - i0 + 1 > M) { i0 = 0; i1 = M - 1; }
-    int n = 0;
-    for (int ii = i0; ii <= i1 && n < maxout; ++ii) {
-        const int i = ((ii % M) + M) % M;
-        const double xm = __dmul_rn(__dadd_rn((double)i, 0.5), dxg);
-        const double d = minimg_d(__dsub_rn(xm, c), L);
-        if (fabs(d) <= half) out[n++] = i;
-    }
-    return n;
 }
 
 __global__ void k_deposit(const double2 *c, const double2 *v, int na, double L, double dxg, double half, int M,
@@ -109,35 +88,6 @@ __global__ void k_vorticity(const double2 *__restrict__ z, int M, double inv2h, 
     const double duy = __dsub_rn(z[(size_t)iy * M + xp].y, z[(size_t)iy * M + xm].y);
     const double dux = __dsub_rn(z[(size_t)yp * M + ix].x, z[(size_t)ym * M + ix].x);
     om[g] = __dsub_rn(__dmul_rn(duy, inv2h), __dmul_rn(dux, inv2h));
-}
-
-// In-place radix-2 FFT (forward, e^{-2 pi i k n / M}) of M complex doubles
-// with stride `stride` between elements and `pitch` between transforms; one
-// block per transform, M/2 threads, data staged in shared memory.
-__global__ void k_fft(double2 *z, int M, int logM, int stride, int pitch)
-{
-    extern __shared__ double2 s[];
-    double2 *base = z + (size_t)blockIdx.x * pitch;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const int r = __brev(i) >> (32 - logM);
-        s[r] = base[(size_t)i * stride];
-    }
-    __syncthreads();
-    for (int len = 2; len <= M; len <<= 1) {
-        const int half = len >> 1;
-        for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
-            const int grp = t / half, pos = t - grp * half;
-            const int i0 = grp * len + pos, i1 = i0 + half;
-            double sn, cs;
-            sincospi(-2.0 * (double)pos / (double)len, &sn, &cs);
-            const double2 a = s[i0], b = s[i1];
-            const double2 wb = make_double2(b.x * cs - b.y * sn, b.x * sn + b.y * cs);
-            s[i0] = make_double2(a.x + wb.x, a.y + wb.y);
-            s[i1] = make_double2(a.x - wb.x, a.y - wb.y);
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < M; i += blockDim.x) base[(size_t)i * stride] = s[i];
 }
 
 __global__ void k_shells(const double2 *Z, int M, double scale, double *E)
@@ -517,8 +467,8 @@ int dpd_energy_spectrum(dpd_ctx *c, int M, double eps, double *E)
     while ((1 << logM) < M) ++logM;
     const size_t sm = 16 * (size_t)M;
     const int thr = M / 2 < 512 ? M / 2 : 512;
-    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, 1, M);   // rows (along x)
-    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, M, 1);   // columns (along y)
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, 1, M, M, 0);   // rows (along x)
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, M, M, 1, 0);   // columns (along y)
     double *dE = (double *)tail;
     CUO(cudaMemsetAsync(dE, 0, 8 * (size_t)(M / 2), c->st));
     const double M2 = (double)M * (double)M;
@@ -772,8 +722,8 @@ extern "C" int dpd_energy_spectrum_noalloc(dpd_ctx *c, int M, double eps, double
     while ((1 << logM) < M) ++logM;
     const size_t sm = 16 * (size_t)M;
     const int thr = M / 2 < 512 ? M / 2 : 512;
-    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, 1, M);
-    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, M, 1);
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, 1, M, M, 0);
+    k_fft<<<M, thr, sm, c->st>>>(z, M, logM, M, M, 1, 0);
     const double M2 = (double)M * (double)M;
     k_shells<<<(M * M + 255) / 256, 256, 0, c->st>>>(z, M, 0.5 / (M2 * M2), dE);
     CUO(cudaGetLastError());

@@ -34,20 +34,11 @@
 
 #include "dpd.h"
 #include "sim_host.h"
+#include "sim3d_host.h"
 #include "sim_kernels.cuh"
 
 namespace dpd {
 
-struct Sys3 {
-    Sys b;                      // geometry scalars, physics, keys, scan/thermo/error words
-    uint4 *S_p, *U_p, *C_p;
-    float4 *S_v, *U_v, *C_v, *C_f;
-    float4 *F;                  // pair-force sums per sorted slot (zero between steps)
-    float4 *S_off;              // offset from the own cell's corner (length units) + id bits, sorted
-    const uint32_t *corner;     // fixed-point corner ceil(c 2^32 / n_c) of cell coordinate c
-    float rc2f;                 // r_c^2 (1 + 1e-5): candidate filter, never narrower than the exact test
-    uint32_t *U_rank, *slot;
-};
 
 __device__ __forceinline__ int cell3(const Sys &d, uint32_t X, uint32_t Y, uint32_t Z)
 {
@@ -350,19 +341,6 @@ __global__ void __launch_bounds__(256) k3_integrate(Sys3 s, int flags)
 
 using namespace dpd;
 
-struct dpd3_ctx {
-    dpd_params p{};
-    Sys3 s{};
-    cudaStream_t st = nullptr;
-    bool own_stream = false;
-    int nscan = 1;
-    void *pool = nullptr;
-    char *stage = nullptr;     // 48 B/bead staging for host state transfers
-    double *h_pin = nullptr;
-    long long step = 0;
-    bool have_state = false;
-};
-
 #define CU3(x)                                                                      \
     do {                                                                            \
         const cudaError_t e_ = (x);                                                 \
@@ -379,6 +357,8 @@ static int latched3(dpd3_ctx *c)
     if (*e & ERR_INTERNAL) return DPD_ERR_INTERNAL;
     return DPD_OK;
 }
+
+int dpd3_internal_latched(dpd3_ctx *c) { return latched3(c); }
 
 static void iteration3(dpd3_ctx *c, int flags)
 {
@@ -462,6 +442,7 @@ void dpd3_destroy(dpd3_ctx *c)
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->pool) cudaFree(c->pool);
+    if (c->obs) cudaFree(c->obs);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;

@@ -221,6 +221,34 @@ class Sim3:
         check(self._lib.dpd3_thermo(self._h, ptr(out)), "dpd3_thermo")
         return out
 
+    # ---------------------------------------------------- observables
+    def velocity_field(self, M: int = 32, eps: float = 0.0):
+        """u_M [iz, iy, ix, 3] and the window counts [iz, iy, ix]."""
+        u = np.zeros((M, M, M, 3), np.float64)
+        n = np.zeros((M, M, M), np.float64)
+        check(self._lib.dpd3_velocity_field(self._h, int(M), float(eps), ptr(u), ptr(n)), "dpd3_velocity_field")
+        return u, n
+
+    def energy_spectrum(self, M: int = 32, eps: float = 0.0):
+        E = np.zeros(M // 2, np.float64)
+        check(self._lib.dpd3_energy_spectrum(self._h, int(M), float(eps), ptr(E)), "dpd3_energy_spectrum")
+        return E
+
+    def vorticity(self, M: int = 32, eps: float = 0.0):
+        """curl u_M [iz, iy, ix, 3]."""
+        om = np.zeros((M, M, M, 3), np.float64)
+        check(self._lib.dpd3_vorticity(self._h, int(M), float(eps), ptr(om)), "dpd3_vorticity")
+        return om
+
+    def velocity_correlation(self, dr: float, nbins: int):
+        g = np.zeros(nbins, np.float64)
+        num = np.zeros(nbins, np.float64)
+        cnt = np.zeros(nbins, np.int64)
+        Li = ctypes.c_double()
+        check(self._lib.dpd3_velocity_correlation(self._h, float(dr), int(nbins), ptr(g), ctypes.byref(Li),
+                                                  ptr(num), ptr(cnt)), "dpd3_velocity_correlation")
+        return g, Li.value, num, cnt
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             self._lib.dpd3_destroy(self._h)

@@ -114,6 +114,15 @@ def ensemble_points(R: int, seed: int = 0):
     return out
 
 
+def sweep_points(L: float = 256.0, phis=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6), gammas=(1.0, 4.5, 20.0),
+                 zetas=(0.01, 0.1, 1.0)):
+    """The parameter sweep of the 256 x 256 box (C2): every (area fraction,
+    gamma, zeta) of the grid, f_p = 1; list of dicts with L, phi, n_dimers,
+    gamma, zeta, fp (other parameters from BASE)."""
+    return [dict(L=float(L), phi=float(p), n_dimers=dimers_for_area_fraction(p, L), gamma=float(g), zeta=float(z),
+                 fp=1.0) for p in phis for g in gammas for z in zetas]
+
+
 def surrogate_points(n: int, seed: int = 0):
     """Parameter rows (area fraction, gamma, zeta, f_p) [n][4] drawn from the
     ranges of the uneven-replica distribution (C4): phi U(0.05, 0.6), gamma

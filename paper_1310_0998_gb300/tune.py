@@ -31,7 +31,7 @@ def autotune(L: float, n_beads: int, x=None, v=None, steps: int = 10, stream=Non
 
 
 def batch_autotune(points, steps: int = 10, stream=None) -> dict:
-    """Time every (tile, variant 2-4) for a batch of replicas (same points as
+    """Time every (tile, variant 2-5) for a batch of replicas (same points as
     Ensemble); the fastest is cached for that replica mix."""
     arr = (DpdParams * len(points))()
     for r, pt in enumerate(points):

@@ -114,3 +114,83 @@ def test_nonfinite_input_reported(Sim3):
         with pytest.raises(DpdError) as e:
             s.set_positions(x, v)
         assert e.value.status == -4
+
+
+# ------------------------------------------------------------ observables
+def _state3(L, nd, seed):
+    x, _ = synth.dimers3(nd, L, 0.5, seed=seed)
+    v = synth.velocities3(2 * nd, 1.0, seed=seed + 10)
+    return x, v
+
+
+@pytest.mark.parametrize("L,nd,M,eps", [(6.0, 324, 8, 0.0), (7.5, 630, 16, 0.0), (10.0, 1500, 16, 2.0),
+                                        (9.0, 1000, 5, 0.0)])
+def test_field_spectrum_vorticity_parity(Sim3, L, nd, M, eps):
+    """Window counts exact, field, E(k) and curl to rounding order against the
+    FP64 oracle on the same canonical state (odd M: field and curl only)."""
+    from oracle import observables as ob
+    x, v = _state3(L, nd, 31)
+    with Sim3(L, 2 * nd, **_kw()) as s:
+        s.set_positions(x, v)
+        s.step(3)
+        xg, vg, _, _ = s.get_state()
+        u, n = s.velocity_field(M, eps)
+        E = s.energy_spectrum(M, eps) if M & (M - 1) == 0 else None
+        om = s.vorticity(M, eps)
+    c, vc = ob.agent_com(xg, vg, L)
+    e = eps if eps > 0 else ob.filter_width3(L, nd)
+    uo, no = ob.velocity_field3(c, vc, L, M, e)
+    np.testing.assert_array_equal(n, no)
+    np.testing.assert_allclose(u, uo, rtol=1e-10, atol=1e-12)
+    if E is not None:
+        Eo = ob.energy_spectrum3(uo)
+        np.testing.assert_allclose(E, Eo, rtol=1e-9, atol=1e-15 * Eo.max())
+    oo = ob.vorticity3(uo, L)
+    np.testing.assert_allclose(om, oo, rtol=1e-9, atol=1e-10 * np.abs(oo).max())
+
+
+@pytest.mark.parametrize("L,nd,dr,nbins", [(6.0, 324, 0.25, 12), (10.0, 1500, 0.5, 20), (8.0, 2000, 0.2, 40)])
+def test_velocity_correlation_parity(Sim3, L, nd, dr, nbins):
+    from oracle import observables as ob
+    x, v = _state3(L, nd, 32)
+    with Sim3(L, 2 * nd, **_kw()) as s:
+        s.set_positions(x, v)
+        s.step(3)
+        xg, vg, _, _ = s.get_state()
+        g, Li, num, cnt = s.velocity_correlation(dr, nbins)
+    c, vc = ob.agent_com(xg, vg, L)
+    go, Lo, numo, cnto = ob.velocity_correlation3(c, vc, L, dr, nbins)
+    np.testing.assert_array_equal(cnt, cnto)
+    np.testing.assert_allclose(num, numo, rtol=1e-10, atol=1e-9)
+    np.testing.assert_allclose(g, go, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(Li, Lo, rtol=1e-8, atol=1e-10)
+
+
+def test_observables_at_density_3(Sim3):
+    """Cube of side 32 at density 3 (49,152 agents): E(k) on 32^3 against the
+    oracle, and the pair counts of the first 16 shells of 0.25 against an
+    exact CPU count (periodic k-d tree candidates, shells by the same FP64
+    expressions)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    from oracle import observables as ob
+    L, nd, M = 32.0, 3 * 32 ** 3 // 2, 32
+    x, v = _state3(L, nd, 33)
+    with Sim3(L, 2 * nd, **_kw()) as s:
+        s.set_positions(x, v)
+        s.step(5)
+        xg, vg, _, _ = s.get_state()
+        E = s.energy_spectrum(M)
+        g, Li, num, cnt = s.velocity_correlation(0.25, 16)
+    c, vc = ob.agent_com(xg, vg, L)
+    uo, _ = ob.velocity_field3(c, vc, L, M, ob.filter_width3(L, nd))
+    np.testing.assert_allclose(E, ob.energy_spectrum3(uo), rtol=1e-9)
+    pairs = spatial.cKDTree(c, boxsize=L).query_pairs(4.0 + 1e-6, output_type="ndarray")
+    d = c[pairs[:, 0]] - c[pairs[:, 1]]
+    d -= L * np.rint(d / L)
+    b = np.floor(np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]) / 0.25)
+    keep = b < 16
+    np.testing.assert_array_equal(cnt, np.bincount(b[keep].astype(np.int64), minlength=16)[:16])
+    dots = (vc[pairs[keep, 0]] * vc[pairs[keep, 1]]).sum(-1)
+    np.testing.assert_allclose(num, np.bincount(b[keep].astype(np.int64), weights=dots, minlength=16)[:16],
+                               rtol=1e-9, atol=1e-9 * np.abs(dots).sum())
+    assert np.isfinite(Li)
