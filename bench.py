@@ -55,6 +55,7 @@ def job_throughput(world: int, units_per_rank: int, steps: int, t_max: float) ->
 CONFIGS = {
     "c3": dict(L=1024.0, n_beads=3 * 1024 * 1024, name="c3: L=1024, density 3, 3,145,728 beads"),
     "c2": dict(L=256.0, n_beads=3 * 256 * 256, name="c2-size: L=256, density 3, 196,608 beads"),
+    "c3q": dict(L=512.0, n_beads=3 * 512 * 512, name="c3-quarter: L=512, density 3, 786,432 beads"),
     "c1": dict(L=32.0, n_beads=1024, name="c1: L=32, 512 dimers"),
 }
 # algorithmic ALU operations of one step, counted on the benchmarked state:
