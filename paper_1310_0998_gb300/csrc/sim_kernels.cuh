@@ -362,9 +362,16 @@ struct TilePlan {
     {
         return (bead_off(nthreads) + (size_t)cap * bead_bytes(count) + 15) & ~size_t(15);
     }
-    static __host__ __device__ size_t bytes(int cap, int nthreads, bool count)
+    // variant 2 on 8 x 8 blocks: the order in which the tile's lanes take
+    // owned beads (u16 each; measured faster there, slower on 16 x 16)
+    static constexpr bool ORDER = VAR == 2 && B == 8;
+    static __host__ __device__ size_t order_off(int cap, int nthreads, bool count)
     {
         return queue_off(cap, nthreads, count) + (size_t)WARP_BYTES * (size_t)(nthreads / 32);
+    }
+    static __host__ __device__ size_t bytes(int cap, int nthreads, bool count)
+    {
+        return order_off(cap, nthreads, count) + (ORDER ? 2 * (size_t)cap : 0);
     }
 };
 
@@ -449,7 +456,11 @@ __device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, in
 
 // Variant 2: pair queue.  Each lane walks the candidates of one owned bead at
 // a time (taking the next bead from a block-wide counter when it runs out, so
-// warps stay balanced); every candidate inside r_c is pushed, packed as
+// warps stay balanced; on 8 x 8 blocks the counter runs through `order`,
+// which lists the beads of the cells that also visit halo cells behind them
+// first, so that the shortest walks come last and the lanes finish closer
+// together); every candidate
+// inside r_c is pushed, packed as
 // (i, j, Newton-3 flag), into the warp's 128-entry buffer.  Whenever 32 pairs
 // are queued the whole warp evaluates them together, so the Philox and force
 // arithmetic runs with every lane active.  Forces land in shared memory
@@ -495,7 +506,7 @@ __device__ __forceinline__ void queue_drain(volatile uint32_t *q, int &qn, EVAL 
 template <int B, bool COUNT>
 __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int th_, const int *s_cbeg,
                                             const int *s_ccnt, const TileArrays &t, volatile uint32_t *q,
-                                            int *s_next, uint32_t s_lo, uint32_t s_hi)
+                                            int *s_next, uint32_t s_lo, uint32_t s_hi, const uint16_t *order)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -517,6 +528,7 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
                 if (k >= n_own) {
                     more = false;
                 } else {
+                    if constexpr (TilePlan<B, 2>::ORDER) k = order[k];
                     xi = t.X[k];
                     const int lx = t.lc[k] & 15, ly = t.lc[k] >> 4;
                     lc0 = (ly + 1) * (B + 2) + lx + 1;
@@ -1147,6 +1159,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     uint32_t *s_items = (uint32_t *)(s_nit + B * B);  // variant 4: the ranges
     const int cap = d.cap;
     const TileArrays t = tile_arrays<B, VAR>(smem, cap, NT, COUNT);
+    uint16_t *s_order = (uint16_t *)(smem + TP::order_off(cap, NT, COUNT));   // variant 2
 
     const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
     const int x0 = tx * B, y0 = ty * B;
@@ -1186,23 +1199,44 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
         s_hcnt[h] = (int)(e - b);
     }
     __syncthreads();
-    if (tid == 0) {
-        int run = n_own;
-        for (int h = 0; h < nh; ++h) {
-            int lx, ly;
-            if (h < tw + 2) { lx = h - 1; ly = -1; }
-            else if (h < 2 * (tw + 2)) { lx = h - (tw + 2) - 1; ly = th_; }
-            else if (h < 2 * (tw + 2) + th_) { lx = -1; ly = h - 2 * (tw + 2); }
-            else { lx = tw; ly = h - 2 * (tw + 2) - th_; }
-            const int lc = (ly + 1) * (B + 2) + lx + 1;
-            s_hbeg[h] = run;
-            s_cbeg[lc] = run;
-            s_ccnt[lc] = s_hcnt[h];
-            run += s_hcnt[h];
+    // halo cells staged after the owned beads: exclusive scan of their
+    // populations by warp 0 (at most 4 B + 4 = 68 cells, three per lane)
+    if (tid < 32) {
+        const int per = (nh + 31) / 32;
+        int local = 0;
+        for (int u = 0; u < per; ++u) {
+            const int h = tid * per + u;
+            if (h < nh) local += s_hcnt[h];
         }
-        s_hbeg[nh] = run;
-        s_sc[0] = run;
-        s_sc[1] = 0;   // next owned bead for the pair queue
+        int incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int w = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += w;
+        }
+        int run = n_own + incl - local;
+        for (int u = 0; u < per; ++u) {
+            const int h = tid * per + u;
+            if (h < nh) {
+                int lx, ly;
+                if (h < tw + 2) { lx = h - 1; ly = -1; }
+                else if (h < 2 * (tw + 2)) { lx = h - (tw + 2) - 1; ly = th_; }
+                else if (h < 2 * (tw + 2) + th_) { lx = -1; ly = h - 2 * (tw + 2); }
+                else { lx = tw; ly = h - 2 * (tw + 2) - th_; }
+                const int lc = (ly + 1) * (B + 2) + lx + 1;
+                s_hbeg[h] = run;
+                s_cbeg[lc] = run;
+                s_ccnt[lc] = s_hcnt[h];
+                run += s_hcnt[h];
+            }
+        }
+        if (tid == 31) {
+            s_hbeg[nh] = n_own + incl;
+            s_sc[0] = n_own + incl;
+            s_sc[1] = 0;   // next owned bead for the pair queue
+            s_sc[2] = 0;   // variant 2 order: beads placed from the front
+            s_sc[3] = 0;   // and from the back
+        }
     }
     __syncthreads();
     const int total = s_sc[0];
@@ -1223,6 +1257,12 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             t.f[4 * k + 3] = 0;
             if (COUNT) t.cnt[k] = 0u;
             t.lc[k] = (unsigned char)(lx | (ly << 4));
+            if constexpr (TP::ORDER) {
+                // cells whose walk also visits halo cells behind them (left
+                // column, bottom row, right column) have the longest walks
+                if (lx == 0 || ly == 0 || lx == tw - 1) s_order[atomicAdd(&s_sc[2], 1)] = (uint16_t)k;
+                else s_order[n_own - 1 - atomicAdd(&s_sc[3], 1)] = (uint16_t)k;
+            }
         }
         for (int k = n_own + tid; k < total; k += NT) {
             int lo = 0, hi = nh - 1;   // last h with hbeg[h] <= k
@@ -1253,7 +1293,8 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             __syncthreads();
             pairs_items<COUNT, 2>(d, n_own, total, tw, t, s_nit, s_items, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi);
         } else {
-            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi);
+            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi,
+                                  s_order);
         }
         __syncthreads();
 
