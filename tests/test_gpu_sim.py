@@ -396,3 +396,34 @@ def test_trajectory_bit_identical_across_kernel_shapes(Sim):
             continue
         for a, b, name in zip(ref, got, ("x", "v", "f")):
             np.testing.assert_array_equal(a, b, err_msg=f"{name} tile={tile} variant={variant}")
+
+
+def test_page_locked_host_buffers(Sim):
+    """Page-locked host buffers (the end-to-end benchmark's) give the same
+    bits as pageable ones: set-up, steps, download and restart."""
+    import torch
+    L, nd = 37.0, 600
+    x, _ = synth.dimers(nd, L, 0.5, seed=12)
+    v = synth.velocities(2 * nd, 1.0, seed=13)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True).numpy()
+        t[:] = a
+        return t
+
+    xp, vp = pinned(x), pinned(v)
+    with Sim(L, 2 * nd, **sim_kw(seed=5)) as a, Sim(L, 2 * nd, **sim_kw(seed=5)) as b:
+        a.set_positions(x, v)
+        b.set_positions(xp, vp)
+        a.step(20)
+        b.step(20)
+        ra = a.get_state()
+        outs = [pinned(np.zeros_like(q)) for q in ra[:3]]
+        rb = b.get_state(*outs)
+        for p, q, name in zip(ra[:3], rb[:3], ("x", "v", "f")):
+            np.testing.assert_array_equal(p, q, err_msg=name)
+        b.set_state(outs[0], outs[1], outs[2], rb[3])
+        a.step(10)
+        b.step(10)
+        for p, q, name in zip(a.get_state()[:3], b.get_state()[:3], ("x", "v", "f")):
+            np.testing.assert_array_equal(p, q, err_msg=name)
