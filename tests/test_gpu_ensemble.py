@@ -163,3 +163,46 @@ def test_profile_runs_the_same_steps(mods):
             np.testing.assert_array_equal(u, w)
     for k in ("scan", "scatter", "force"):
         assert ph[k + "_ms"] > 0 and 0 < ph[k + "_busy_ms"] <= ph[k + "_ms"] * 1.05, ph
+
+
+def test_full_size_c4_batch(mods, orc):
+    """The 256-replica uneven batch (box side U(32, 192), area fraction
+    U(0.05, 0.6), gamma log-U(0.5, 50), zeta log-U(0.005, 2), f_p U(0.5, 2);
+    4.7 M beads) in the bench's launch configuration (16 x 16 cell blocks,
+    pair queue): the set-up forces of four replicas spread over the sizes
+    against the FP64 cell-list oracle (||dF|| / ||F|| and max_i |dF_i| /
+    max(|F_i|, F_rms) within 1e-5), and after 20 batched steps every replica
+    equals, bit for bit, the same replica restarted alone from its initial
+    canonical state."""
+    Ensemble, Sim = mods
+    pts = []
+    for r, e in enumerate(synth.ensemble_points(256, 0)):
+        pts.append(dict(a=25.0, kBT=1.0, rc=1.0, k_bond=100.0, r0=0.5, dt=0.01, L=e["L"], n_beads=2 * e["n_dimers"],
+                        gamma=e["gamma"], zeta=e["zeta"], f_p=e["fp"], seed=r, replica=r, tile=16, variant=2))
+    with Ensemble(pts) as ens:
+        ens.init_random(0)
+        ens.sync()
+        init = [ens.replica(r).get_state() for r in range(len(pts))]
+        ens.step(20)
+        ens.sync()
+        got = [ens.replica(r).get_state()[:3] for r in range(len(pts))]
+    for r in (0, 85, 170, 255):
+        x, v, f, st = init[r]
+        p = pts[r]
+        op = orc.params(L=p["L"], a=p["a"], gamma=p["gamma"], kBT=p["kBT"], rc=p["rc"], kbond=p["k_bond"], r0=p["r0"],
+                        fp=p["f_p"], zeta=p["zeta"], dt=p["dt"], seed=p["seed"], replica=p["replica"])
+        fo, _ = orc.forces(op, x, v.astype(np.float64), st, cells=True)
+        fn = np.linalg.norm(fo, axis=1)
+        frms = float(np.sqrt(np.mean(fn ** 2)))
+        err = np.linalg.norm(f.astype(np.float64) - fo, axis=1)
+        assert np.linalg.norm(err) / np.linalg.norm(fo) <= 1e-5, r
+        assert np.max(err / np.maximum(fn, frms)) <= 1e-5, r
+    for r, p in enumerate(pts):
+        kw = {k: v for k, v in p.items() if k not in ("L", "n_beads")}
+        with Sim(p["L"], p["n_beads"], **kw) as s:
+            x, v, f, st = init[r]
+            s.set_state(x, v, f, st)
+            s.step(20)
+            alone = s.get_state()[:3]
+        for a, b, name in zip(got[r], alone, ("x", "v", "f")):
+            np.testing.assert_array_equal(a, b, err_msg=f"replica {r} {name}")
