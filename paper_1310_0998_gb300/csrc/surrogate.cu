@@ -273,15 +273,23 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
 // Fused forward pass of one member for 128-row tiles, persistent (one CTA per
 // SM).  The CTA stages W1, W2, W3 once as K-major core matrices (8, 128 and
 // 24 KB) and keeps them in shared memory; per tile the inputs go into the
-// activation buffer (64 KB), layer l runs as tcgen05.mma into tensor memory
-// (256 columns), and the epilogue reads the accumulator back (16 warps: warp
-// w takes rows 32 (w % 4) .. +31 and a quarter of the columns), adds the
-// bias, applies SiLU and writes the BF16 activations
-// into the same buffer in the operand layout of the next layer; only the 48
-// output columns go to global memory.  231,632 bytes of shared memory.
+// activation buffer (64 KB) and each layer runs as tcgen05.mma into one of two
+// 256-column tensor-memory accumulators, alternating from layer to layer.  The
+// epilogue of a layer reads its accumulator back in four chunks of 64 columns
+// (16 warps: warp w takes rows 32 (w % 4) .. +31 and 16 of the chunk's
+// columns), adds the bias, applies SiLU and writes the BF16 activations into
+// the activation buffer in the operand layout of the next layer; as soon as a
+// chunk is written, one thread issues the next layer's products over those 64
+// K columns into the other accumulator, so the tensor cores work while the
+// warps run the rest of the epilogue.  A warp signals a written chunk on the
+// chunk's mbarrier and goes on (its tensor-memory load of the next chunk is
+// already in flight); only the issuing thread waits for all 16 warps.  The
+// next tile's first layer is issued before the last layer's 48 output columns
+// are read back and stored.  231,664 bytes of shared memory, 512
+// tensor-memory columns.
 constexpr int FW_W1 = NH * NIN_P * 2, FW_W2 = NH * NH * 2, FW_W3 = NOUT_P * NH * 2, FW_ACT = TC_M * NH * 2;
 constexpr int FW_BIAS = (NH + NH + NOUT_P) * 4;
-constexpr int FW_SMEM = FW_W1 + FW_W2 + FW_W3 + FW_ACT + FW_BIAS + 16;
+constexpr int FW_SMEM = FW_W1 + FW_W2 + FW_W3 + FW_ACT + FW_BIAS + 48;
 
 // [rows x K] K-contiguous BF16 (leading dimension ld) -> K-major core
 // matrices: 16-byte chunk (r, c) at ((r/8) (K/8) + c) 128 + (r%8) 16.
@@ -295,22 +303,6 @@ __device__ __forceinline__ void stage_kmajor(unsigned char *dst, const __nv_bflo
     }
 }
 
-// One layer's products, issued by a single thread: D[128 x N] = A[128 x K] B[N x K]^T.
-__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, int K, int N, uint32_t mbar)
-{
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t idesc = tc_idesc(TC_M, N), sbo = (uint32_t)(K >> 3) * 128u;
-    for (int ks = 0; ks < (K >> 4); ++ks) {
-        const uint64_t ad = tc_desc(a + ks * 256, 128, sbo), bd = tc_desc(b + ks * 256, 128, sbo);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
-        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
-                 : "memory");
-}
-
 // tcgen05.ld of 16 columns of this warp's lane quadrant; the registers are
 // valid only after tmem_wait, which takes them as operands so that no use can
 // be scheduled before it.
@@ -322,46 +314,6 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t addr, uint32_t *r)
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                    "=r"(r[15])
                  : "r"(addr));
-}
-
-// 32 columns of this warp's lane quadrant in one load (the CTA has registers
-// to spare: one 256-thread CTA per SM)
-__device__ __forceinline__ void tmem_ld32_sync(uint32_t addr, uint32_t *r)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                 "tcgen05.wait::ld.sync.aligned;"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(addr)
-                 : "memory");
-}
-
-// 32 columns, issue only: the registers become valid at tmem_wait32
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t addr, uint32_t *r)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void tmem_wait32(uint32_t *r)
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :: "memory");
 }
 
 __device__ __forceinline__ void tmem_wait(uint32_t *r)
@@ -385,14 +337,40 @@ __device__ __forceinline__ float silu_fast(float z)
     return fmaf(h, t, h);
 }
 
-// 32 accumulator columns (+ bias) -> SiLU -> BF16, stored as four 16-byte
-// chunks of this thread's row in the K-major operand layout.
-__device__ __forceinline__ void silu_store32(const uint32_t *u, const float *bias, unsigned char *row, int c0)
+// K steps [ks0, ks1) of one layer's products, issued by a single thread:
+// D[128 x N] (+)= A[128 x K] B[N x K]^T, the first K step overwriting D.
+__device__ __forceinline__ void mma_range(uint32_t tmem, uint32_t a, uint32_t b, int K, int N, int ks0, int ks1)
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t idesc = tc_idesc(TC_M, N), sbo = (uint32_t)(K >> 3) * 128u;
+    for (int ks = ks0; ks < ks1; ++ks) {
+        const uint64_t ad = tc_desc(a + ks * 256, 128, sbo), bd = tc_desc(b + ks * 256, 128, sbo);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+// Epilogue of a 256-column accumulator in four chunks of 64 columns: warp w
+// reads 16 columns (64 q + 16 (w / 4) ..) of lane quadrant w % 4 (the load of
+// chunk q + 1 in flight while chunk q is processed), adds the bias, applies
+// SiLU, stores BF16 into K chunks 8 q + 2 (w / 4) and the next of the K = 256
+// operand tile, and arrives on chunk q's mbarrier (16 arrivals complete it).
+// After each chunk `issue(q)` runs on every thread of the warp (it acts on
+// thread 0 only), then the warp reconverges.
+__device__ __forceinline__ void silu_store16(const uint32_t *u, const float *bias, unsigned char *row, int c0)
 {
     const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
-    uint32_t h[16];
+    uint32_t h[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4; ++j) {
         const float4 b = b4[j];
         const __nv_bfloat162 p0 = __floats2bfloat162_rn(silu_fast(__uint_as_float(u[4 * j]) + b.x),
                                                         silu_fast(__uint_as_float(u[4 * j + 1]) + b.y));
@@ -401,30 +379,46 @@ __device__ __forceinline__ void silu_store32(const uint32_t *u, const float *bia
         h[2 * j] = *reinterpret_cast<const uint32_t *>(&p0);
         h[2 * j + 1] = *reinterpret_cast<const uint32_t *>(&p1);
     }
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-        *reinterpret_cast<uint4 *>(row + ((c0 >> 3) + g) * 128) = make_uint4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+    *reinterpret_cast<uint4 *>(row + (c0 >> 3) * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(row + ((c0 >> 3) + 1) * 128) = make_uint4(h[4], h[5], h[6], h[7]);
 }
 
-// Accumulator + bias -> SiLU -> BF16 activations in the K = 256 operand layout
-// of the next layer.  16 warps: warp w reads the rows of lane quadrant w % 4
-// (tcgen05.ld reaches only its own quadrant) and the column quarter w / 4 (64
-// columns, two loads of 32; the second is in flight while the first chunk's
-// arithmetic runs).
-__device__ __forceinline__ void epi_silu(uint32_t tmem, const float *bias, unsigned char *act)
+template <typename ISSUE>
+__device__ __forceinline__ void epi_silu_streamed(uint32_t tmem, const float *bias, unsigned char *act,
+                                                  uint32_t cbar, ISSUE issue)
 {
-    const int warp = threadIdx.x >> 5, q = warp & 3, part = warp >> 2;
-    const int r = 32 * q + (threadIdx.x & 31);
-    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
-    const int cb = part * (NH / 4);
+    const int warp = threadIdx.x >> 5, qd = warp & 3, part = warp >> 2, lane = threadIdx.x & 31;
+    const int r = 32 * qd + lane;
+    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * part);
     unsigned char *row = act + (r & 7) * 16 + (r >> 3) * (NH / 8) * 128;
-    uint32_t u0[32], u1[32];
-    tmem_ld32_issue(tb + (uint32_t)cb, u0);
-    tmem_wait32(u0);
-    tmem_ld32_issue(tb + (uint32_t)(cb + 32), u1);
-    silu_store32(u0, bias, row, cb);
-    tmem_wait32(u1);
-    silu_store32(u1, bias, row, cb + 32);
+    uint32_t ua[16], ub[16];
+    tmem_ld16_issue(tb, ua);
+    tmem_wait(ua);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t *cur = (q & 1) ? ub : ua;
+        uint32_t *nxt = (q & 1) ? ua : ub;
+        if (q < 3) tmem_ld16_issue(tb + (uint32_t)(64 * (q + 1)), nxt);
+        silu_store16(cur, bias, row, 64 * q + 16 * part);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(cbar + 8u * (uint32_t)q)
+                         : "memory");
+        issue(q);
+        __syncwarp();
+        if (q < 3) tmem_wait(nxt);
+    }
+}
+
+// Writers' shared-memory stores become visible to the tensor cores' reads,
+// and tensor-memory accesses before the barrier are ordered before those after.
+__device__ __forceinline__ void tc_block_sync()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
 constexpr int FW_THREADS = 512;
@@ -440,16 +434,21 @@ __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat1
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sW1 = sm, *sW2 = sm + FW_W1, *sW3 = sW2 + FW_W2, *sAct = sW3 + FW_W3;
     float *sb = reinterpret_cast<float *>(sAct + FW_ACT);   // b1[256], b2[256], b3[48]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + NH + NH + NOUT_P);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sb + NH + NH + NOUT_P);   // [0] products, [1..4] chunks
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 5);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t mb = smem_u32(mbar);
+    const uint32_t mb = smem_u32(mbar), cbar = mb + 8u;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(tslot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(tslot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        for (int q = 0; q < 4; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(cbar + 8u * (uint32_t)q), "r"(FW_THREADS / 32)
+                         : "memory");
+    }
     stage_kmajor(sW1, W1, NH, NIN_P, NIN_P);
     stage_kmajor(sW2, W2, NH, NH, NH);
     stage_kmajor(sW3, W3, NOUT_P, NH, NH);
@@ -461,8 +460,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat1
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t aA = smem_u32(sAct), a1 = smem_u32(sW1), a2 = smem_u32(sW2), a3 = smem_u32(sW3);
-    uint32_t parity = 0;
+    uint32_t parity = 0, eph = 0;   // phases of the products' and of the chunks' mbarriers
     bool ok = true;
+    // the two accumulators, used in turn by the layers of consecutive tiles
+    auto acc = [&](int g) { return tmem + (uint32_t)((g & 1) * NH); };
     // the 128 x 16 input block of a tile is 256 chunks of 16 bytes, one per
     // thread: chunk (row tid / 2, column half tid % 2); the next tile's chunk is
     // loaded into registers while the current tile runs its three layers
@@ -471,66 +472,92 @@ __global__ void __launch_bounds__(FW_THREADS, 1) k_mlp_fwd_tc(const __nv_bfloat1
     const bool xin = tid < XCH;
     const int xr = (tid & (XCH - 1)) >> 1, xc = tid & 1;
     const int xoff = ((xr >> 3) * 2 + xc) * 128 + (xr & 7) * 16;
-    uint4 xcur = make_uint4(0u, 0u, 0u, 0u);
-    if (xin && blockIdx.x < ntiles)
-        xcur = *reinterpret_cast<const uint4 *>(X0 + (size_t)(blockIdx.x * TC_M + xr) * NIN_P + 8 * xc);
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int m0 = tile * TC_M;
-        if (xin) *reinterpret_cast<uint4 *>(sAct + xoff) = xcur;
-        uint4 xnext = make_uint4(0u, 0u, 0u, 0u);
-        if (xin && tile + (int)gridDim.x < ntiles)
-            xnext = *reinterpret_cast<const uint4 *>(X0 + (size_t)((tile + gridDim.x) * TC_M + xr) * NIN_P + 8 * xc);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-#pragma unroll 1
-        for (int layer = 0; layer < 3; ++layer) {
-            if (tid == 0) {
-                if (layer == 0) mma_layer(tmem, aA, a1, NIN_P, NH, mb);
-                else if (layer == 1) mma_layer(tmem, aA, a2, NH, NH, mb);
-                else mma_layer(tmem, aA, a3, NH, NOUT_P, mb);
-            }
-            // one decision for the whole CTA (barriers follow)
-            if (__syncthreads_or(tc_wait(mb, parity) ? 0 : 1)) {
-                ok = false;
-                if (tid == 0) atomicOr(err, 1);
-                tc_wait(mb, parity);   // second bounded wait for MMAs still in flight
-                break;
-            }
-            parity ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (layer < 2) {
-                epi_silu(tmem, sb + layer * NH, sAct);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            } else {
-                // 48 output columns: 16 for each of the column parts 0, 1, 2
-                const int q = warp & 3, part = warp >> 2;
-                const int row = m0 + 32 * q + lane;
-                const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
-                if (part < NOUT_P / 16) {
-                    const int c0 = 16 * part;
-                    uint32_t u[16];
-                    tmem_ld16_issue(tb + (uint32_t)c0, u);
-                    tmem_wait(u);
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(u[j]);
-                    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)row * NOUT_P + c0);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        dst[j] = make_float4(v[4 * j] + sb[2 * NH + c0 + 4 * j], v[4 * j + 1] + sb[2 * NH + c0 + 4 * j + 1],
-                                             v[4 * j + 2] + sb[2 * NH + c0 + 4 * j + 2],
-                                             v[4 * j + 3] + sb[2 * NH + c0 + 4 * j + 3]);
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();   // accumulator and activation buffer free for the next layer / tile
+    // one decision for the whole CTA (barriers follow); on a timeout the
+    // error is flagged and the products still in flight are waited for once more
+    auto wait_all = [&]() {
+        if (__syncthreads_or(tc_wait(mb, parity) ? 0 : 1)) {
+            if (tid == 0) atomicOr(err, 1);
+            tc_wait(mb, parity);
+            return false;
         }
-        xcur = xnext;
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return true;
+    };
+    int g = 0;
+    int tile = blockIdx.x;
+    if (tile < ntiles) {
+        if (xin) *reinterpret_cast<uint4 *>(sAct + xoff) =
+            *reinterpret_cast<const uint4 *>(X0 + (size_t)(tile * TC_M + xr) * NIN_P + 8 * xc);
+        tc_block_sync();
+        if (tid == 0) {
+            mma_range(acc(g), aA, a1, NIN_P, NH, 0, 1);
+            mma_commit(mb);
+        }
+    }
+    for (; tile < ntiles && ok; tile += gridDim.x) {
+        const int m0 = tile * TC_M;
+        const bool more = tile + (int)gridDim.x < ntiles;
+        uint4 xnext = make_uint4(0u, 0u, 0u, 0u);
+        if (xin && more)
+            xnext = *reinterpret_cast<const uint4 *>(X0 + (size_t)((tile + gridDim.x) * TC_M + xr) * NIN_P + 8 * xc);
+        // layer 1's epilogue, streaming layer 2's products
+        if (!(ok = wait_all())) break;
+        epi_silu_streamed(acc(g), sb, sAct, cbar, [&](int q) {
+            if (tid == 0) {
+                if (!tc_wait(cbar + 8u * (uint32_t)q, eph)) atomicOr(err, 2);
+                mma_range(acc(g + 1), aA, a2, NH, NH, 4 * q, 4 * q + 4);
+            }
+        });
+        eph ^= 1u;
+        if (tid == 0) mma_commit(mb);
+        // layer 2's epilogue, streaming layer 3's products (its reads of the
+        // activation buffer are over once layer 2's products have completed)
+        if (!(ok = wait_all())) break;
+        epi_silu_streamed(acc(g + 1), sb + NH, sAct, cbar, [&](int q) {
+            if (tid == 0) {
+                if (!tc_wait(cbar + 8u * (uint32_t)q, eph)) atomicOr(err, 2);
+                mma_range(acc(g + 2), aA, a3, NH, NOUT_P, 4 * q, 4 * q + 4);
+            }
+        });
+        eph ^= 1u;
+        if (tid == 0) mma_commit(mb);
+        if (!(ok = wait_all())) break;
+        // the next tile's first layer, then this tile's 48 output columns
+        if (more) {
+            if (xin) *reinterpret_cast<uint4 *>(sAct + xoff) = xnext;
+            tc_block_sync();
+            if (tid == 0) {
+                mma_range(acc(g + 3), aA, a1, NIN_P, NH, 0, 1);
+                mma_commit(mb);
+            }
+        }
+        {
+            const int qd = warp & 3, part = warp >> 2;
+            const int row = m0 + 32 * qd + lane;
+            const uint32_t tb = acc(g + 2) + ((uint32_t)(32 * qd) << 16);
+            if (part < NOUT_P / 16) {
+                const int c0 = 16 * part;
+                uint32_t u[16];
+                tmem_ld16_issue(tb + (uint32_t)c0, u);
+                tmem_wait(u);
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(u[j]);
+                float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)row * NOUT_P + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    dst[j] = make_float4(v[4 * j] + sb[2 * NH + c0 + 4 * j], v[4 * j + 1] + sb[2 * NH + c0 + 4 * j + 1],
+                                         v[4 * j + 2] + sb[2 * NH + c0 + 4 * j + 2],
+                                         v[4 * j + 3] + sb[2 * NH + c0 + 4 * j + 3]);
+            }
+        }
+        g += 3;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
 }
 
 // The training products on the tensor cores: the same C = A B^T and
