@@ -66,6 +66,8 @@ OPS_TEST, OPS_PAIR, OPS_BEAD = 8.0, 110.0, 70.0
 BYTES_PER_BEAD_STEP = 36.0     # algorithmic HBM bytes per bead-step (read 20, write 16)
 LANES = 128                    # FP32/INT32 lanes per SM
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "force_traffic_c3.md")
+ISSUE_PROFILE = os.path.join(ROOT, "profiles", "force_issue_c3q.md")
+SCHEDULERS = 4                 # warp schedulers per SM
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1310_0998_gb300", "csrc", f)
                   for f in ("sim_kernels.cuh", "dpd_device.cuh", "sim.cu")]
 
@@ -83,13 +85,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(tile: int, variant: int):
-    """DRAM bytes per force-kernel launch from the committed ncu summary, if
-    it was taken on this exact kernel source and shape; else None."""
-    if not os.path.exists(TRAFFIC_PROFILE):
+def profile_record(path: str, key: str, tile: int, variant: int):
+    """A value from a committed ncu summary (its `- key: value` lines), if it
+    was taken on this exact kernel source and shape; else None."""
+    if not os.path.exists(path):
         return None
     kv = {}
-    for line in open(TRAFFIC_PROFILE):
+    for line in open(path):
         if line.startswith("- ") and ": " in line:
             k, v = line[2:].split(": ", 1)
             kv[k.strip()] = v.strip().strip("`")
@@ -98,9 +100,20 @@ def measured_traffic(tile: int, variant: int):
             return None
         if int(kv["tile"]) != tile or int(kv["variant"]) != variant:
             return None
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
+
+
+def measured_traffic(tile: int, variant: int):
+    """DRAM bytes per force-kernel launch at C3 (ncu, body step)."""
+    return profile_record(TRAFFIC_PROFILE, "dram_bytes_per_launch", tile, variant)
+
+
+def measured_warp_inst_per_bead(tile: int, variant: int):
+    """Warp instructions the force kernel executes per bead (ncu, body step of
+    a density-3 box; the count per bead does not depend on the box size)."""
+    return profile_record(ISSUE_PROFILE, "warp_inst_per_bead", tile, variant)
 
 
 def algorithmic_ops(counts: np.ndarray, pairs: int, n_beads: int):
@@ -671,8 +684,16 @@ def main():
     alu_peak = n_sm * LANES * pk["sm_max_mhz"] * 1e6
     alu_ach = ops_step / force_s
     hbm_ach = BYTES_PER_BEAD_STEP * value / world / 1e9
-    traffic = measured_traffic(info.tile, info.variant) if cfg["name"].startswith("c3") and args.wexp in (0.0, 2.0) \
+    traffic = measured_traffic(info.tile, info.variant) if cfg["name"].startswith("c3:") and args.wexp in (0.0, 2.0) \
         else None
+    wipb = measured_warp_inst_per_bead(info.tile, info.variant) if args.wexp in (0.0, 2.0) else None
+    issue = None
+    if wipb is not None:
+        slots = n_sm * SCHEDULERS * force_s * pk["sm_max_mhz"] * 1e6
+        issue = {"warp_inst_per_bead": wipb, "frac": wipb * nb / slots,
+                 "note": "warp instructions per bead from the committed ncu summary (this kernel source) x beads / "
+                         "(SMs x 4 schedulers x the force kernel's event time x max SM clock): the share of issue "
+                         "slots the kernel fills, the bound that binds"}
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
@@ -693,7 +714,7 @@ def main():
                                   "counted on the benchmarked state",
                      "peak_src": f"{n_sm} SMs x {LANES} lanes x {pk['sm_max_mhz']:.0f} MHz (max SM clock, "
                                  f"{pk['src']} peaks file)",
-                     "ms": force_s * 1e3},
+                     "ms": force_s * 1e3, "issue": issue},
         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": pk["hbm"], "frac": hbm_ach / pk["hbm"],
                 "bytes_per_bead_step": BYTES_PER_BEAD_STEP, "peak_src": pk["src"]},
         "kernels_ms": {"scan": float(prof[:, 0].mean()), "scatter": float(prof[:, 1].mean()),
