@@ -116,8 +116,10 @@ __device__ __forceinline__ unsigned long long gtimer()
 // the phase to its arrival at the barrier into tlog[(3 s + p) gridDim + b],
 // and block 0 writes the global timer at each barrier release into
 // tlog[3 nsteps gridDim + 4 s + i] (i = 0 at the step's start).
+// 16 x 16 blocks: five CTAs per SM fit in shared memory, so the register
+// budget of five is used (no spills); smaller blocks keep eight.
 template <int B, int VAR>
-__global__ void __launch_bounds__(TILE_THREADS, 8)
+__global__ void __launch_bounds__(TILE_THREADS, B == 16 ? 5 : 8)
     k_ensemble(const Sys *__restrict__ sys, const uint32_t *__restrict__ scan_items, int n_scan,
                const uint32_t *__restrict__ scat, int n_scat, const uint32_t *__restrict__ tiles, int n_tiles,
                unsigned *bar, int *berr, int nsteps, int final_last, unsigned long long *ctr,
