@@ -405,15 +405,20 @@ def three_d_leg(steps=20, warmup=3, L=64.0, seed=0):
         for _ in range(3):
             s.energy_spectrum(64)
         spec_ms = (time.perf_counter() - t0) / 3 * 1e3
+        s.velocity_correlation(0.25, 16)
+        t0 = time.perf_counter()
+        _, _, _, vcnt = s.velocity_correlation(0.25, 16)
+        vcf_ms = (time.perf_counter() - t0) * 1e3
     rate = nb * steps / dt
     pk = peaks()
     alu_peak = sm_count() * LANES * pk["sm_max_mhz"] * 1e6
     return {"beads": nb, "L": L, "steps": steps, "particle_steps_per_s": rate, "ms_per_step": 1e3 * dt / steps,
             "roofline": {"bound": "alu", "achieved": OPS_PER_BEAD_STEP_3D * rate / 1e12, "peak": alu_peak / 1e12,
                          "unit": "Tops/s", "frac": OPS_PER_BEAD_STEP_3D * rate / alu_peak},
-            "spectrum_M": 64, "spectrum_ms": spec_ms,
+            "spectrum_M": 64, "spectrum_ms": spec_ms, "vcf_r4_ms": vcf_ms, "vcf_r4_pairs": int(vcnt.sum()),
             "timing": "wall clock around synchronised steps (scan, scatter, pair forces, integration per step); "
-                      "spectrum: per synchronising call (COM, windowed field on 64^3, FFT, shells)"}
+                      "spectrum: per synchronising call (COM, windowed field on 64^3, FFT, shells); velocity "
+                      "correlation r < 4 (16 shells): per call (cell grid)"}
 
 
 def surrogate_leg(n_train=2000, n_test=200, n_noise=50, seed=0, keep=False):

@@ -378,11 +378,14 @@ int dpd3_energy_spectrum(dpd3_ctx *ctx, int M, double eps, double *E);
 /* omega [M^3][3] = curl u_M by second-order central differences on the
  * periodic grid of spacing L/M; 3 <= M <= 256. */
 int dpd3_vorticity(dpd3_ctx *ctx, int M, double eps, double *omega);
-/* Velocity correlation over all agent pairs a < b with COM separation
+/* Velocity correlation over the agent pairs a < b with COM separation
  * r = sqrt((dx^2 + dy^2) + dz^2) (minimum image) in bin floor(r / dr) <
  * nbins (1 <= nbins <= 4096): g [nbins] as in dpd_velocity_correlation (NaN
  * for an empty bin), *L_int by the trapezoid rule, num / cnt the raw sums
- * and pair counts (may be NULL).  O(N_agents^2) work. */
+ * and pair counts (may be NULL).  The pairs within r_max = nbins dr come from
+ * a periodic cell grid of side >= r_max when at least three such cells fit
+ * per side (at most 256), else from all agent pairs (O(N_agents^2)); counts
+ * and sums are the same either way. */
 int dpd3_velocity_correlation(dpd3_ctx *ctx, double dr, int nbins, double *g, double *L_int, double *num,
                               int64_t *cnt);
 

@@ -1,7 +1,8 @@
 // Device pieces shared by the two- and three-dimensional observables
 // (Secs. 5.3-5.4 of arXiv:1310.0998): the minimum image in FP64, the grid
-// points whose filter window holds a coordinate, and a radix-2 FFT along one
-// axis of a complex grid.
+// points whose filter window holds a coordinate, a radix-2 FFT along one
+// axis of a complex grid, and the single-block scan of the velocity
+// correlation's cell counts.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -61,6 +62,31 @@ static __global__ void k_fft(double2 *z, int M, int logM, long long stride, int 
         __syncthreads();
     }
     for (int i = threadIdx.x; i < M; i += blockDim.x) base[(long long)i * stride] = s[i];
+}
+
+// Exclusive scan of n counts in one block (n up to a few million): each
+// thread sums a contiguous run, a block scan of the run sums, then the runs.
+static __global__ void k_vcf_scan(const unsigned *cnt, int n, unsigned *start)
+{
+    __shared__ unsigned s_sum[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int per = (n + T - 1) / T, b = t * per, e = min(n, b + per);
+    unsigned sum = 0;
+    for (int i = b; i < e; ++i) sum += cnt[i];
+    s_sum[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        const unsigned v = t >= o ? s_sum[t - o] : 0u;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    unsigned run = s_sum[t] - sum;
+    for (int i = b; i < e; ++i) {
+        start[i] = run;
+        run += cnt[i];
+    }
+    if (t == T - 1) start[n] = s_sum[t];
 }
 
 }  // namespace dpd

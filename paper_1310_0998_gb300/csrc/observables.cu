@@ -238,31 +238,6 @@ __global__ void k_vcf_count(const double2 *c, int na, double cw, int ncv, unsign
     rank[k] = atomicAdd(&cnt[cell], 1u);
 }
 
-// Exclusive scan of n counts in one block (n up to a few million): each
-// thread sums a contiguous run, a block scan of the run sums, then the runs.
-__global__ void k_vcf_scan(const unsigned *cnt, int n, unsigned *start)
-{
-    __shared__ unsigned s_sum[1024];
-    const int T = blockDim.x, t = threadIdx.x;
-    const int per = (n + T - 1) / T, b = t * per, e = min(n, b + per);
-    unsigned sum = 0;
-    for (int i = b; i < e; ++i) sum += cnt[i];
-    s_sum[t] = sum;
-    __syncthreads();
-    for (int o = 1; o < T; o <<= 1) {
-        const unsigned v = t >= o ? s_sum[t - o] : 0u;
-        __syncthreads();
-        s_sum[t] += v;
-        __syncthreads();
-    }
-    unsigned run = s_sum[t] - sum;
-    for (int i = b; i < e; ++i) {
-        start[i] = run;
-        run += cnt[i];
-    }
-    if (t == T - 1) start[n] = s_sum[t];
-}
-
 __global__ void k_vcf_scatter(const double2 *c, const double2 *v, int na, double cw, int ncv, const unsigned *start,
                               const unsigned *rank, double2 *sc, double2 *sv)
 {

@@ -16,8 +16,9 @@
 //                 k -> -k maps a shell onto itself, so the shell sum of
 //                 |Z1|^2 + |Z2|^2 equals M^6 times that of the three |uhat|^2
 //   omega         curl u_M by second-order central differences
-//   g_v, L_gv     all agent pairs a < b: bin floor(r / dr) of the COM
-//                 separation r = sqrt((dx^2 + dy^2) + dz^2), sums of v_a . v_b;
+//   g_v, L_gv     agent pairs a < b within r_max: bin floor(r / dr) of the
+//                 COM separation r = sqrt((dx^2 + dy^2) + dz^2), sums of
+//                 v_a . v_b (a cell grid of side >= r_max, or all pairs);
 //                 g_v(b) = (<v_a . v_b>_b - |<v>|^2) / (<|v|^2> - |<v>|^2),
 //                 L_gv by the trapezoid rule over r = 0 (g = 1) and the
 //                 centres of the non-empty bins
@@ -245,6 +246,136 @@ __global__ void __launch_bounds__(VCF3_TILE) k3_vcf(const D4 *c, const D4 *v, in
     }
 }
 
+// Pairs within r_max only: agents counting-sorted into a periodic grid of
+// n_v^3 cells of side cw >= r_max (z-major), one block per cell taking its
+// agents against its own cell (b after a) and the 13 forward neighbours
+// (dz > 0, or dz = 0 and dy > 0, or dz = dy = 0 and dx > 0), staged in
+// shared memory in chunks.  The shell is taken from FP32 offsets to the
+// block's cell corner where r / dr lies at least 1e-3 from a shell edge and
+// from r_max, else by the FP64 expressions of k3_vcf, so every pair lands in
+// the shell the all-pairs pass gives it; per-warp FP64 histograms.
+constexpr int VCF3C_THREADS = 128, VCF3C_CHUNK = 256, VCF3C_WARPS = VCF3C_THREADS / 32;
+
+__device__ __forceinline__ int vcf3_cell(const D4 &p, double cw, int nv)
+{
+    auto one = [&](double x) {
+        const int c = (int)floor(__ddiv_rn(x, cw));
+        return c < 0 ? 0 : (c >= nv ? nv - 1 : c);
+    };
+    return (one(p.z) * nv + one(p.y)) * nv + one(p.x);
+}
+
+__global__ void k3_vcf_count(const D4 *c, int na, double cw, int nv, unsigned *cnt, unsigned *rank)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    rank[k] = atomicAdd(&cnt[vcf3_cell(c[k], cw, nv)], 1u);
+}
+
+__global__ void k3_vcf_scatter(const D4 *c, const D4 *v, int na, double cw, int nv, const unsigned *start,
+                               const unsigned *rank, D4 *sc, D4 *sv)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const D4 p = c[k];
+    const unsigned dst = start[vcf3_cell(p, cw, nv)] + rank[k];
+    if (dst < (unsigned)na) {
+        sc[dst] = p;
+        sv[dst] = v[k];
+    }
+}
+
+__global__ void __launch_bounds__(VCF3C_THREADS) k3_vcf_cells(const D4 *sc, const D4 *sv, const unsigned *start,
+                                                              int nv, double L, double cw, double dr, int nbins,
+                                                              double *gnum, unsigned long long *gcnt)
+{
+    extern __shared__ __align__(32) unsigned char smem3c[];
+    D4 *bc = (D4 *)smem3c;                                                   // [VCF3C_CHUNK]
+    D4 *bv = bc + VCF3C_CHUNK;
+    float4 *bo = (float4 *)(bv + VCF3C_CHUNK);
+    double *snum = (double *)(bo + VCF3C_CHUNK);                             // [VCF3C_WARPS][nbins]
+    unsigned long long *scnt = (unsigned long long *)(snum + VCF3C_WARPS * nbins);
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < VCF3C_WARPS * nbins; i += blockDim.x) { snum[i] = 0.0; scnt[i] = 0ull; }
+    const int cell = blockIdx.x, cz = cell / (nv * nv), cy = (cell / nv) % nv, cx = cell % nv;
+    const unsigned a0 = start[cell], a1 = start[cell + 1];
+    const double ox = cx * cw, oy = cy * cw, oz = cz * cw, hL = 0.5 * L;
+    const double rmax2 = (double)nbins * dr * (double)nbins * dr * (1.0 + 1e-9);
+    const float rscr = (float)(nbins * dr) * 1.0001f + 1e-4f * (float)cw, rscr2 = rscr * rscr;
+    const float inv_drf = (float)(1.0 / dr), nbf = (float)nbins;
+    double *wnum = snum + warp * nbins;
+    unsigned long long *wcnt = scnt + warp * nbins;
+    for (int nb = 0; nb < 14; ++nb) {
+        // nb = 0: own cell; 1..13: the forward half of the 26 neighbours
+        int dxc = 0, dyc = 0, dzc = 0;
+        if (nb > 0) {
+            const int o = nb + 13;   // offsets 14..26 of the 3 x 3 x 3 block in z-major order
+            dzc = o / 9 - 1;
+            dyc = (o / 3) % 3 - 1;
+            dxc = o % 3 - 1;
+        }
+        int nx = cx + dxc, ny = cy + dyc, nz = cz + dzc;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        if (nx >= nv) { nx -= nv; sx = L; } else if (nx < 0) { nx += nv; sx = -L; }
+        if (ny >= nv) { ny -= nv; sy = L; } else if (ny < 0) { ny += nv; sy = -L; }
+        if (nz >= nv) { nz -= nv; sz = L; }
+        const int nc = (nz * nv + ny) * nv + nx;
+        const unsigned b0 = start[nc], b1 = start[nc + 1];
+        for (unsigned c0 = b0; c0 < b1; c0 += VCF3C_CHUNK) {
+            const int m = (int)min((unsigned)VCF3C_CHUNK, b1 - c0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                const D4 p = sc[c0 + q];
+                bc[q] = p;
+                bv[q] = sv[c0 + q];
+                bo[q] = make_float4((float)(p.x + sx - ox), (float)(p.y + sy - oy), (float)(p.z + sz - oz), 0.f);
+            }
+            __syncthreads();
+            for (unsigned a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                const D4 ca = sc[a], va = sv[a];
+                const float ax = (float)(ca.x - ox), ay = (float)(ca.y - oy), az = (float)(ca.z - oz);
+                const int q0 = nb == 0 ? (int)max(0ll, (long long)a + 1 - (long long)c0) : 0;
+                for (int q = q0; q < m; ++q) {
+                    const float fx = ax - bo[q].x, fy = ay - bo[q].y, fz = az - bo[q].z;
+                    const float r2f = fx * fx + fy * fy + fz * fz;
+                    if (r2f >= rscr2) continue;
+                    const float tf = sqrtf(r2f) * inv_drf;
+                    const float fl = floorf(tf);
+                    int bin;
+                    if (tf - fl > 1e-3f && fl + 1.0f - tf > 1e-3f && tf < nbf - 1e-3f) {
+                        bin = (int)fl;
+                    } else {
+                        const D4 cb = bc[q];
+                        double dx = __dsub_rn(ca.x, cb.x), dy = __dsub_rn(ca.y, cb.y), dz = __dsub_rn(ca.z, cb.z);
+                        dx = dx > hL ? __dsub_rn(dx, L) : (dx < -hL ? __dadd_rn(dx, L) : dx);
+                        dy = dy > hL ? __dsub_rn(dy, L) : (dy < -hL ? __dadd_rn(dy, L) : dy);
+                        dz = dz > hL ? __dsub_rn(dz, L) : (dz < -hL ? __dadd_rn(dz, L) : dz);
+                        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                        if (!(r2 < rmax2)) continue;
+                        const double bf = floor(__ddiv_rn(sqrt(r2), dr));
+                        if (!(bf < (double)nbins)) continue;
+                        bin = (int)bf;
+                    }
+                    const D4 vb = bv[q];
+                    atomicAdd(&wnum[bin], __dadd_rn(__dadd_rn(__dmul_rn(va.x, vb.x), __dmul_rn(va.y, vb.y)),
+                                                    __dmul_rn(va.z, vb.z)));
+                    atomicAdd(&wcnt[bin], 1ull);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        double sn = 0.0;
+        unsigned long long cn = 0ull;
+        for (int w = 0; w < VCF3C_WARPS; ++w) { sn += snum[w * nbins + b]; cn += scnt[w * nbins + b]; }
+        if (cn) {
+            atomicAdd(&gnum[b], sn);
+            atomicAdd(&gcnt[b], cn);
+        }
+    }
+}
+
 }  // namespace dpd
 
 using namespace dpd;
@@ -383,11 +514,22 @@ int dpd3_velocity_correlation(dpd3_ctx *c, double dr, int nbins, double *g, doub
     if (!c->have_state) return DPD_ERR_STATE;
     const int na = c->s.b.n / 2;
     const double L = c->p.L;
+    // a cell grid of side >= r_max when at least three cells fit per side (and
+    // the grid stays below 16.8 M cells), else all agent pairs; both decide a
+    // pair's shell with the same FP64 expressions
+    const double rmax = (double)nbins * dr * (1.0 + 1e-9);
+    const double nv_d = std::floor(L / rmax);
+    const bool cells = nv_d >= 3.0 && nv_d <= 256.0;
+    const int nv = cells ? (int)nv_d : 0;
+    const size_t ncell = (size_t)nv * nv * nv;
     const long long ntile = (na + VCF3_TILE - 1) / VCF3_TILE, nblk = ntile * (ntile + 1) / 2;
-    if (nblk > 2147483647ll) return DPD_ERR_INVALID_ARG;
+    if (!cells && nblk > 2147483647ll) return DPD_ERR_INVALID_ARG;
     auto up = [](size_t o) { return (o + 255) & ~size_t(255); };
     const size_t o_cc = 0, o_vv = up(32 * (size_t)na), o_num = up(o_vv + 32 * (size_t)na),
-                 o_cnt = up(o_num + 8 * (size_t)nbins), o_acc = up(o_cnt + 8 * (size_t)nbins), bytes = o_acc + 256;
+                 o_cnt = up(o_num + 8 * (size_t)nbins), o_acc = up(o_cnt + 8 * (size_t)nbins),
+                 o_ccnt = up(o_acc + 256), o_cst = up(o_ccnt + 4 * ncell), o_rnk = up(o_cst + 4 * (ncell + 1)),
+                 o_scs = up(o_rnk + (cells ? 4 * (size_t)na : 0)), o_svs = up(o_scs + (cells ? 32 * (size_t)na : 0)),
+                 bytes = up(o_svs + (cells ? 32 * (size_t)na : 0));
     char *b = scratch3(c, bytes);
     if (!b) return DPD_ERR_OOM;
     D4 *cc = (D4 *)(b + o_cc), *vv = (D4 *)(b + o_vv);
@@ -398,10 +540,24 @@ int dpd3_velocity_correlation(dpd3_ctx *c, double dr, int nbins, double *g, doub
     CUO3(cudaMemsetAsync(acc, 0, 64, c->st));
     k3_agent_com<<<(na + 255) / 256, 256, 0, c->st>>>(c->s.C_p, c->s.C_v, na, L, c->s.b.ulen_d, cc, vv);
     k3_vmeans<<<64, 256, 0, c->st>>>(vv, na, acc);
-    const size_t sm = 16 * (size_t)nbins + 32 + 64 * VCF3_TILE;
-    if (sm > 200 * 1024) return DPD_ERR_INVALID_ARG;
-    CUO3(cudaFuncSetAttribute(k3_vcf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k3_vcf<<<(unsigned)nblk, VCF3_TILE, sm, c->st>>>(cc, vv, na, L, dr, nbins, gnum, gcnt);
+    if (cells) {
+        const double cw = L / nv;
+        unsigned *ccnt = (unsigned *)(b + o_ccnt), *cst = (unsigned *)(b + o_cst), *rnk = (unsigned *)(b + o_rnk);
+        D4 *scs = (D4 *)(b + o_scs), *svs = (D4 *)(b + o_svs);
+        CUO3(cudaMemsetAsync(ccnt, 0, 4 * ncell, c->st));
+        k3_vcf_count<<<(na + 255) / 256, 256, 0, c->st>>>(cc, na, cw, nv, ccnt, rnk);
+        k_vcf_scan<<<1, 1024, 0, c->st>>>(ccnt, (int)ncell, cst);
+        k3_vcf_scatter<<<(na + 255) / 256, 256, 0, c->st>>>(cc, vv, na, cw, nv, cst, rnk, scs, svs);
+        const size_t sm = (size_t)VCF3C_CHUNK * 80 + (size_t)VCF3C_WARPS * nbins * 16;
+        if (sm > 200 * 1024) return DPD_ERR_INVALID_ARG;
+        CUO3(cudaFuncSetAttribute(k3_vcf_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k3_vcf_cells<<<(unsigned)ncell, VCF3C_THREADS, sm, c->st>>>(scs, svs, cst, nv, L, cw, dr, nbins, gnum, gcnt);
+    } else {
+        const size_t sm = 16 * (size_t)nbins + 32 + 64 * VCF3_TILE;
+        if (sm > 200 * 1024) return DPD_ERR_INVALID_ARG;
+        CUO3(cudaFuncSetAttribute(k3_vcf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k3_vcf<<<(unsigned)nblk, VCF3_TILE, sm, c->st>>>(cc, vv, na, L, dr, nbins, gnum, gcnt);
+    }
     CUO3(cudaGetLastError());
     std::vector<double> hn(nbins), ha(4);
     std::vector<unsigned long long> hc(nbins);

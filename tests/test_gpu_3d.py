@@ -149,7 +149,10 @@ def test_field_spectrum_vorticity_parity(Sim3, L, nd, M, eps):
     np.testing.assert_allclose(om, oo, rtol=1e-9, atol=1e-10 * np.abs(oo).max())
 
 
-@pytest.mark.parametrize("L,nd,dr,nbins", [(6.0, 324, 0.25, 12), (10.0, 1500, 0.5, 20), (8.0, 2000, 0.2, 40)])
+@pytest.mark.parametrize("L,nd,dr,nbins", [
+    (6.0, 324, 0.25, 12), (10.0, 1500, 0.5, 20), (8.0, 2000, 0.2, 40),      # r_max >= L/3: all agent pairs
+    (10.0, 1500, 0.25, 12), (16.0, 4000, 0.3, 10),                          # cell grids of 3^3 and 5^3
+    (12.0, 3000, 0.2, 19)])                                                  # 3^3, r_max not a cell multiple
 def test_velocity_correlation_parity(Sim3, L, nd, dr, nbins):
     from oracle import observables as ob
     x, v = _state3(L, nd, 32)
@@ -168,9 +171,9 @@ def test_velocity_correlation_parity(Sim3, L, nd, dr, nbins):
 
 def test_observables_at_density_3(Sim3):
     """Cube of side 32 at density 3 (49,152 agents): E(k) on 32^3 against the
-    oracle, and the pair counts of the first 16 shells of 0.25 against an
-    exact CPU count (periodic k-d tree candidates, shells by the same FP64
-    expressions)."""
+    oracle, and the pair counts of the first 16 shells of 0.25 (the cell-grid
+    pass, 8^3 cells) against an exact CPU count (periodic k-d tree
+    candidates, shells by the same FP64 expressions)."""
     spatial = pytest.importorskip("scipy.spatial")
     from oracle import observables as ob
     L, nd, M = 32.0, 3 * 32 ** 3 // 2, 32
