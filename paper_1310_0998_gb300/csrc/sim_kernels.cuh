@@ -348,7 +348,9 @@ struct TilePlan {
     static constexpr int NH = 4 * B + 4;            // halo cells
     static constexpr int NITEM = (VAR == 4 || VAR == 5) ? B * B * (FLAT_MAXI + 1) : 0;
     static constexpr int NINT = 2 * NCL + 3 * (NH + 1) + 8 + NITEM;
-    static constexpr int QLEN = VAR == 4 ? 64 : 128;            // queue entries per warp
+    // queue entries per warp: a drain starts at 32 and a round pushes at most
+    // two per lane, so 31 + 64 entries are the most a queue holds
+    static constexpr int QLEN = VAR == 4 ? 64 : 96;
     static constexpr int WARP_BYTES = 4 * QLEN + (VAR == 4 ? 16 * 32 : 0);
     static __host__ __device__ size_t red_off() { return ((size_t)NINT * 4 + 7) & ~size_t(7); }
     static __host__ __device__ size_t bead_off(int nthreads)
@@ -362,12 +364,20 @@ struct TilePlan {
     {
         return (bead_off(nthreads) + (size_t)cap * bead_bytes(count) + 15) & ~size_t(15);
     }
+    // variant 2: per owned cell, its walk descriptor (local cell index, the
+    // neighbour cells owned by the tile and the ones it visits), so a lane
+    // starting a bead reads it instead of deriving it
+    static constexpr bool DESC = VAR == 2;
+    static __host__ __device__ size_t desc_off(int cap, int nthreads, bool count)
+    {
+        return queue_off(cap, nthreads, count) + (size_t)WARP_BYTES * (size_t)(nthreads / 32);
+    }
     // variant 2 on 8 x 8 blocks: the order in which the tile's lanes take
     // owned beads (u16 each; measured faster there, slower on 16 x 16)
     static constexpr bool ORDER = VAR == 2 && B == 8;
     static __host__ __device__ size_t order_off(int cap, int nthreads, bool count)
     {
-        return queue_off(cap, nthreads, count) + (size_t)WARP_BYTES * (size_t)(nthreads / 32);
+        return desc_off(cap, nthreads, count) + (DESC ? 4 * (size_t)(B * B) : 0);
     }
     static __host__ __device__ size_t bytes(int cap, int nthreads, bool count)
     {
@@ -504,9 +514,9 @@ __device__ __forceinline__ void queue_drain(volatile uint32_t *q, int &qn, EVAL 
 }
 
 template <int B, bool COUNT>
-__device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int th_, const int *s_cbeg,
-                                            const int *s_ccnt, const TileArrays &t, volatile uint32_t *q,
-                                            int *s_next, uint32_t s_lo, uint32_t s_hi, const uint16_t *order)
+__device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, const int *s_cbeg, const int *s_ccnt,
+                                            const TileArrays &t, volatile uint32_t *q, int *s_next, uint32_t s_lo,
+                                            uint32_t s_hi, const uint32_t *desc, const uint16_t *order)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -530,14 +540,12 @@ __device__ __forceinline__ void pairs_queue(const Sys &d, int n_own, int tw, int
                 } else {
                     if constexpr (TilePlan<B, 2>::ORDER) k = order[k];
                     xi = t.X[k];
-                    const int lx = t.lc[k] & 15, ly = t.lc[k] >> 4;
-                    lc0 = (ly + 1) * (B + 2) + lx + 1;
+                    const uint32_t lcb = t.lc[k];
+                    const uint32_t dsc = desc[(lcb >> 4) * B + (lcb & 15u)];
+                    lc0 = (int)(dsc & 0x1ffu);
+                    own = (dsc >> 9) & 0x1ffu;
+                    visit = dsc >> 18;
                     pid = d.excl ? (t.id[k] ^ 1u) : 0xffffffffu;
-                    // which neighbour cells are owned by this tile (Newton-3 side)
-                    const uint32_t px = lx < tw - 1, nx = lx > 0, py = ly < th_ - 1, ny = ly > 0;
-                    own = 1u | (px << 1) | ((px & py) << 2) | (py << 3) | ((nx & py) << 4) | (nx << 5) |
-                          ((nx & ny) << 6) | (ny << 7) | ((px & ny) << 8);
-                    visit = 0x1fu | (~own & 0x1e0u);   // cells behind only when they are halo
                 }
             }
             if (more) {
@@ -1160,6 +1168,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const int cap = d.cap;
     const TileArrays t = tile_arrays<B, VAR>(smem, cap, NT, COUNT);
     uint16_t *s_order = (uint16_t *)(smem + TP::order_off(cap, NT, COUNT));   // variant 2
+    uint32_t *s_desc = (uint32_t *)(smem + TP::desc_off(cap, NT, COUNT));     // variant 2
 
     const int ty = tile / d.ntx, tx = tile - ty * d.ntx;
     const int x0 = tx * B, y0 = ty * B;
@@ -1175,13 +1184,22 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     const uint32_t g1 = max(g0, min(d.cstart[base + tw * th_], n));
     const int n_own = (int)(g1 - g0);
 
-    // owned cell table
+    // owned cell table (and, for variant 2, each owned cell's walk
+    // descriptor: local cell index, the neighbour cells the tile owns (the
+    // Newton-3 side) and the ones to visit (ahead always, behind only when
+    // halo))
     for (int c = tid; c < tw * th_; c += NT) {
         const int ly = c / tw, lx = c - ly * tw;
         const uint32_t b = min(max(d.cstart[base + c], g0), g1), e = min(max(d.cstart[base + c + 1], b), g1);
         const int lc = (ly + 1) * (B + 2) + lx + 1;
         s_cbeg[lc] = (int)(b - g0);
         s_ccnt[lc] = (int)(e - b);
+        if constexpr (TP::DESC) {
+            const uint32_t px = lx < tw - 1, nx = lx > 0, py = ly < th_ - 1, ny = ly > 0;
+            const uint32_t own = 1u | (px << 1) | ((px & py) << 2) | (py << 3) | ((nx & py) << 4) | (nx << 5) |
+                                 ((nx & ny) << 6) | (ny << 7) | ((px & ny) << 8);
+            s_desc[ly * B + lx] = (uint32_t)lc | (own << 9) | ((0x1fu | (~own & 0x1e0u)) << 18);
+        }
     }
     // halo cell table
     for (int h = tid; h < nh; h += NT) {
@@ -1293,7 +1311,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             __syncthreads();
             pairs_items<COUNT, 2>(d, n_own, total, tw, t, s_nit, s_items, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi);
         } else {
-            pairs_queue<B, COUNT>(d, n_own, tw, th_, s_cbeg, s_ccnt, t, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi,
+            pairs_queue<B, COUNT>(d, n_own, s_cbeg, s_ccnt, t, (uint32_t *)wbuf, s_sc + 1, s_lo, s_hi, s_desc,
                                   s_order);
         }
         __syncthreads();
