@@ -16,17 +16,20 @@
 //   counts, cstart  cell populations and their exclusive scan (the same
 //                   decoupled look-back scan as the 2D path)
 //   C_p, C_v, C_f   canonical (X_s, v_s, f_s) in id order after each call
-//   F    float4[N]  pair-force sums of the current step by sorted slot (kept
-//                   zero between steps)
+//   F    s64[N][4]  pair-force sums of the current step by sorted slot, in
+//                   fixed point (2^-24 force units per count, as the 2D
+//                   path), kept zero between steps
 // One step: scan, scatter, pair forces, integration.  The pair kernel gives
 // one thread per bead the half stencil (the rest of its cell and the 13
 // cells ahead of it), so every pair inside r_c is evaluated once; the pairs
 // go through a warp queue so that their arithmetic runs on full warps, the
 // force lands on the owner through shared memory and its reaction on the
-// partner through one float4 atomic into F (sorted order).  The integration
-// kernel reads and clears F, adds bond, propulsion and drag, does the second
-// half-kick, the FP64 thermo partials, the next half-kick and drift, and bins
-// the new position.
+// partner through 64-bit integer atomics into F (sorted order).  Every sum is
+// in fixed point, so it does not depend on the order in which pairs are met
+// and a run is reproducible bit for bit.  The integration kernel reads and
+// clears F, adds bond, propulsion and drag, does the second half-kick, the
+// FP64 thermo partials, the next half-kick and drift, and bins the new
+// position.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -128,10 +131,11 @@ __device__ __forceinline__ float pair_scalar3(const Sys &d, float r2, float rinv
 }
 
 // One queued pair (sorted slot q, owner lane o of this warp): the pair force
-// on the owner, accumulated in shared memory, and its reaction on q, added to
-// q's sum in global memory (Newton-3: every pair is evaluated once).
+// on the owner, accumulated in shared memory ((hi, lo) words per component,
+// as the 2D tile), and its reaction on q, added to q's 64-bit sums in global
+// memory (Newton-3: every pair is evaluated once).
 __device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const uint4 *pis, const float4 *vis,
-                                      float (*fs)[4], uint32_t s_lo, uint32_t s_hi)
+                                      int (*fs)[6], uint32_t s_lo, uint32_t s_hi)
 {
     const Sys &d = s.b;
     if (q >= (uint32_t)d.n) {   // cannot happen: every queued slot was read below n
@@ -147,10 +151,15 @@ __device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const ui
     const float ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;   // e = (x_i - x_j)/r
     const float dve = (vi.x - vj.x) * ex + (vi.y - vj.y) * ey + (vi.z - vj.z) * ez;
     const float F = pair_scalar3(d, r2, rinv, dve, pi.w, pj.w, s_lo, s_hi);
-    atomicAdd(&fs[o][0], F * ex);
-    atomicAdd(&fs[o][1], F * ey);
-    atomicAdd(&fs[o][2], F * ez);
-    atomicAdd(&s.F[q], make_float4(-F * ex, -F * ey, -F * ez, 0.f));
+    if (!(fabsf(F) < FQ_MAX)) set_err(d, ERR_NONFINITE);
+    const long long qx = fq(F * ex), qy = fq(F * ey), qz = fq(F * ez);
+    fq_add(&fs[o][0], qx);
+    fq_add(&fs[o][2], qy);
+    fq_add(&fs[o][4], qz);
+    unsigned long long *fq_q = (unsigned long long *)(s.F + 4 * (size_t)q);
+    atomicAdd(fq_q, (unsigned long long)-qx);
+    atomicAdd(fq_q + 1, (unsigned long long)-qy);
+    atomicAdd(fq_q + 2, (unsigned long long)-qz);
 }
 
 // Pair forces, one thread per bead over the half stencil: the rest of its own
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(256, 5) k3_pairs(Sys3 s)
     __shared__ unsigned char s_ql[8][64];
     __shared__ uint4 s_pi[8][32];
     __shared__ float4 s_vi[8][32];
-    __shared__ float s_f[8][32][4];
+    __shared__ int s_f[8][32][6];
     const bool active = g < d.n;
     const long long step = *d.step;
     const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xffffffffull);
@@ -180,9 +189,8 @@ __global__ void __launch_bounds__(256, 5) k3_pairs(Sys3 s)
     const uint32_t id = pi.w, pid = d.excl ? (id ^ 1u) : 0xffffffffu;
     s_pi[warp][lane] = pi;
     s_vi[warp][lane] = vi;
-    s_f[warp][lane][0] = 0.f;
-    s_f[warp][lane][1] = 0.f;
-    s_f[warp][lane][2] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_f[warp][lane][c] = 0;
     __syncwarp();
     const int cx = cell_coord(d, pi.x), cy = cell_coord(d, pi.y), cz = cell_coord(d, pi.z);
     // the walk tests separations from cell-corner offsets (no conversion per
@@ -246,7 +254,14 @@ __global__ void __launch_bounds__(256, 5) k3_pairs(Sys3 s)
     }
     if (lane < qn) eval3(s, s_q[warp][lane], s_ql[warp][lane], s_pi[warp], s_vi[warp], s_f[warp], s_lo, s_hi);
     __syncwarp();
-    if (active) atomicAdd(&s.F[g], make_float4(s_f[warp][lane][0], s_f[warp][lane][1], s_f[warp][lane][2], 0.f));
+    if (active) {
+        unsigned long long *fq_g = (unsigned long long *)(s.F + 4 * (size_t)g);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long qc = (long long)s_f[warp][lane][2 * c] * 65536ll + (long long)(unsigned)s_f[warp][lane][2 * c + 1];
+            if (qc) atomicAdd(fq_g + c, (unsigned long long)qc);
+        }
+    }
 }
 
 // Everything after the pair sums, one thread per sorted slot: the pair force
@@ -257,15 +272,17 @@ __global__ void __launch_bounds__(256) k3_integrate(Sys3 s, int flags)
 {
     const Sys &d = s.b;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    float ke = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+    double ke = 0.0, px = 0.0, py = 0.0, pz = 0.0;
     const uint32_t n = (uint32_t)d.n;
     if (g < d.n) {
         const uint4 pi = s.S_p[g];
         const float4 vi = s.S_v[g];
         const uint32_t id = pi.w;
-        const float4 fp = s.F[g];
-        s.F[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float fx = fp.x, fy = fp.y, fz = fp.z;
+        longlong2 *fqg = (longlong2 *)(s.F + 4 * (size_t)g);
+        const longlong2 f01 = fqg[0], f23 = fqg[1];
+        fqg[0] = make_longlong2(0ll, 0ll);
+        fqg[1] = make_longlong2(0ll, 0ll);
+        float fx = fq_to_f(f01.x), fy = fq_to_f(f01.y), fz = fq_to_f(f23.x);
         // bond and propulsion (partner id ^ 1), drag on the half-step velocity
         const uint32_t ps = s.slot[id ^ 1u];
         if (ps < n) {
@@ -288,8 +305,11 @@ __global__ void __launch_bounds__(256) k3_integrate(Sys3 s, int flags)
         fy -= d.zeta * vy;
         fz -= d.zeta * vz;
         if (!(flags & F_FIRST)) { vx += d.hdtm * fx; vy += d.hdtm * fy; vz += d.hdtm * fz; }
-        ke = vx * vx + vy * vy + vz * vz;
-        px = vx; py = vy; pz = vz;
+        {
+            const double dvx = (double)vx, dvy = (double)vy, dvz = (double)vz;
+            ke = fma(dvx, dvx, fma(dvy, dvy, dvz * dvz));
+            px = dvx; py = dvy; pz = dvz;
+        }
         if (flags & F_FINAL) {
             s.C_p[id] = make_uint4(pi.x, pi.y, pi.z, 0u);
             s.C_v[id] = make_float4(vx, vy, vz, 0.f);
@@ -315,7 +335,8 @@ __global__ void __launch_bounds__(256) k3_integrate(Sys3 s, int flags)
             s.U_v[g] = make_float4(vx, vy, vz, 0.f);
         }
     }
-    // thermo partials: FP32 within a warp, FP64 across warps and blocks
+    // thermo partials in FP64 throughout (per bead, across the warp, across
+    // warps and blocks)
     if (flags & (F_ADVANCE | F_FINAL)) {
         for (int o = 16; o > 0; o >>= 1) {
             ke += __shfl_xor_sync(0xffffffffu, ke, o);
@@ -402,7 +423,7 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
                  o_slot = take(4 * n), o_cnt = take(4 * nce), o_cst = take(4 * (nce + 1)),
                  o_th = take(32 * (size_t)THERMO_CAP), o_step = take(8), o_err = take(4), o_einfo = take(32),
                  o_ss = take(8 * (size_t)c->nscan), o_tk = take(8), o_stage = take(48 * n),
-                 o_F = take(16 * n), o_off = take(16 * n), o_corner = take(4 * (size_t)nc);
+                 o_F = take(32 * n), o_off = take(16 * n), o_corner = take(4 * (size_t)nc);
     if (cudaMalloc(&c->pool, off) != cudaSuccess || cudaMallocHost((void **)&c->h_pin, 4096) != cudaSuccess) {
         dpd3_destroy(c);
         return DPD_ERR_OOM;
@@ -412,7 +433,7 @@ int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out)
     c->s.U_p = (uint4 *)(b + o_Up); c->s.U_v = (float4 *)(b + o_Uv);
     c->s.C_p = (uint4 *)(b + o_Cp); c->s.C_v = (float4 *)(b + o_Cv); c->s.C_f = (float4 *)(b + o_Cf);
     c->s.U_rank = (uint32_t *)(b + o_rank); c->s.slot = (uint32_t *)(b + o_slot);
-    c->s.F = (float4 *)(b + o_F);   // zeroed with the pool; k3_integrate keeps it zero between steps
+    c->s.F = (long long *)(b + o_F);   // zeroed with the pool; k3_integrate keeps it zero between steps
     c->s.S_off = (float4 *)(b + o_off);
     c->s.corner = (const uint32_t *)(b + o_corner);
     c->s.rc2f = (float)(p->rc * p->rc * (1.0 + 1e-5));

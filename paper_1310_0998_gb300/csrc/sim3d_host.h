@@ -13,7 +13,8 @@ struct Sys3 {
     Sys b;                      // geometry scalars, physics, keys, scan/thermo/error words
     uint4 *S_p, *U_p, *C_p;
     float4 *S_v, *U_v, *C_v, *C_f;
-    float4 *F;                  // pair-force sums per sorted slot (zero between steps)
+    long long *F;               // pair-force sums per sorted slot: x, y, z counts of 2^-24
+                                // force units and a pad word (zero between steps)
     float4 *S_off;              // offset from the own cell's corner (length units) + id bits, sorted
     const uint32_t *corner;     // fixed-point corner ceil(c 2^32 / n_c) of cell coordinate c
     float rc2f;                 // r_c^2 (1 + 1e-5): candidate filter, never narrower than the exact test
