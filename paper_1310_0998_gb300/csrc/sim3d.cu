@@ -335,25 +335,25 @@ __global__ void __launch_bounds__(256) k3_integrate(Sys3 s, int flags)
             s.U_v[g] = make_float4(vx, vy, vz, 0.f);
         }
     }
-    // thermo partials in FP64 throughout (per bead, across the warp, across
-    // warps and blocks)
+    // thermo partials in FP64 throughout (per bead, across the block, across
+    // blocks).  One bead per thread, so the block sum goes through shared
+    // memory: warp c adds quantity c (eight values per lane, then across its
+    // lanes), a quarter of the FP64 additions of a shuffle tree in every warp
+    // (the FP64 pipe is narrow on this part).
     if (flags & (F_ADVANCE | F_FINAL)) {
-        for (int o = 16; o > 0; o >>= 1) {
-            ke += __shfl_xor_sync(0xffffffffu, ke, o);
-            px += __shfl_xor_sync(0xffffffffu, px, o);
-            py += __shfl_xor_sync(0xffffffffu, py, o);
-            pz += __shfl_xor_sync(0xffffffffu, pz, o);
-        }
-        __shared__ double red[8][4];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) { red[wid][0] = ke; red[wid][1] = px; red[wid][2] = py; red[wid][3] = pz; }
+        __shared__ double red[4][256];
+        const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+        red[0][tid] = ke;
+        red[1][tid] = px;
+        red[2][tid] = py;
+        red[3][tid] = pz;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double a[4] = {0, 0, 0, 0};
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-                for (int c = 0; c < 4; ++c) a[c] += red[w][c];
-            double *t = d.thermo + 4 * (size_t)(*d.step % THERMO_CAP);
-            for (int c = 0; c < 4; ++c) atomicAdd(&t[c], a[c]);
+        if (wid < 4) {
+            double a = 0.0;
+            for (int i = lane; i < (int)blockDim.x; i += 32) a += red[wid][i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) atomicAdd(&d.thermo[4 * (size_t)(*d.step % THERMO_CAP) + wid], a);
         }
     }
 }
