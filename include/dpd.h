@@ -335,10 +335,12 @@ void dpd_tune_clear(void);
  * in a periodic cube of side p->L (fixed-point positions per axis, n_c^3
  * cells of side L / n_c >= r_c).  The paper itself simulates two dimensions.
  * All of dpd_params applies (tile and variant are ignored).  Host pointers.
+ * Pair forces are summed in fixed point as in two dimensions, so a run
+ * repeats bit for bit; the thermo sums are FP64.
  * ------------------------------------------------------------------------ */
 typedef struct dpd3_ctx dpd3_ctx;
 
-/* Create on the current device (about 190 bytes per bead plus 8 per cell). */
+/* Create on the current device (about 220 bytes per bead plus 8 per cell). */
 int dpd3_create(const dpd_params *p, void *stream, dpd3_ctx **out);
 void dpd3_destroy(dpd3_ctx *ctx);
 
