@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(TILE_THREADS, B == 16 ? 5 : 8)
             Thermo3 th{0.0, 0.0, 0.0};
             force_tile<B, false, VAR>(d, (int)(w & 0x3fffffu), flags, smem, th);
             __syncthreads();
-            thermo_flush(d, th, (double *)(smem + tile_red_off<B, VAR>()));
+            thermo_flush_tile(d, th, (double *)(smem + tile_flush_off<B, VAR>()));
             __syncthreads();
         }
         if (lg) tlog[(3ull * s + 2) * nb + blockIdx.x] = gtimer() - t0;

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 10) k_force(Sys d, int flags)
     force_tile<B, COUNT, VAR>(d, blockIdx.x, flags, smem, th);
     if (flags & (F_ADVANCE | F_FINAL)) {
         __syncthreads();
-        thermo_flush(d, th, (double *)(smem + tile_red_off<B, VAR>()));
+        thermo_flush_tile(d, th, (double *)(smem + tile_flush_off<B, VAR>()));
     }
 }
 

@@ -1329,12 +1329,36 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
     }
 }
 
-// Shared-memory offset of the thermo reduction buffer of a variant's tile plan.
+// Shared-memory offset of a buffer of 3 x TILE_THREADS doubles that is free
+// once a tile's integration has finished (the staged bead arrays).
 template <int B, int VAR>
-__host__ __device__ inline size_t tile_red_off()
+__host__ __device__ inline size_t tile_flush_off()
 {
-    if constexpr (VAR == 3) return TilePlanG<B>::red_off();
-    else return TilePlan<B, VAR>::red_off();
+    if constexpr (VAR == 3) return TilePlanG<B>::bead_off(TILE_THREADS);
+    else return TilePlan<B, VAR>::bead_off(TILE_THREADS);
+}
+
+// Block reduction of a tile's thermo partials into the FP64 ring slot of
+// `step` (FP64 throughout): every thread's partials to shared memory (buf,
+// 3 blockDim doubles), then warp q adds quantity q (blockDim / 32 values per
+// lane, then across its lanes) and adds it to the slot.  A third of the FP64
+// additions of a shuffle tree in every warp (the FP64 pipe is narrow on this
+// part).  buf is read by warps 0-2 after the call: the caller synchronises
+// before reusing it.
+__device__ __forceinline__ void thermo_flush_tile(const Sys &d, Thermo3 th, double *buf)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
+    buf[tid] = th.ke;
+    buf[nt + tid] = th.px;
+    buf[2 * nt + tid] = th.py;
+    __syncthreads();
+    if (wid < 3) {
+        double a = 0.0;
+        for (int i = lane; i < nt; i += 32) a += buf[wid * nt + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) atomicAdd(&d.thermo[4 * (size_t)(*d.step % THERMO_CAP) + wid], a);
+    }
 }
 
 // Block reduction of the thermo partials into the FP64 ring slot of `step`
