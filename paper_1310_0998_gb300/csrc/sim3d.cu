@@ -153,9 +153,9 @@ __device__ __forceinline__ void eval3(const Sys3 &s, uint32_t q, int o, const ui
     const float F = pair_scalar3(d, r2, rinv, dve, pi.w, pj.w, s_lo, s_hi);
     if (!(fabsf(F) < FQ_MAX)) set_err(d, ERR_NONFINITE);
     const long long qx = fq(F * ex), qy = fq(F * ey), qz = fq(F * ez);
-    fq_add(&fs[o][0], qx);
-    fq_add(&fs[o][2], qy);
-    fq_add(&fs[o][4], qz);
+    fq_add(&fs[o][0], 1, qx);
+    fq_add(&fs[o][2], 1, qy);
+    fq_add(&fs[o][4], 1, qz);
     unsigned long long *fq_q = (unsigned long long *)(s.F + 4 * (size_t)q);
     atomicAdd(fq_q, (unsigned long long)-qx);
     atomicAdd(fq_q + 1, (unsigned long long)-qy);

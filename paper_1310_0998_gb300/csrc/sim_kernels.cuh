@@ -205,15 +205,16 @@ constexpr float FQ_INV = 5.9604644775390625e-08f;    // 2^-24
 constexpr float FQ_MAX = 65536.0f;
 __device__ __forceinline__ long long fq(float g) { return __float2ll_rn(__fmul_rn(g, FQ_SCALE)); }
 __device__ __forceinline__ float fq_to_f(long long q) { return __fmul_rn(__ll2float_rn(q), FQ_INV); }
-// a: the (hi, lo) words of one force component in shared memory
-__device__ __forceinline__ void fq_add(int *a, long long q)
+// a: the hi word of one force component in shared memory, its lo word `fs`
+// words further on
+__device__ __forceinline__ void fq_add(int *a, int fs, long long q)
 {
     atomicAdd(a, (int)(q >> 16));
-    atomicAdd((unsigned *)(a + 1), (unsigned)(q & 0xffffll));
+    atomicAdd((unsigned *)(a + fs), (unsigned)(q & 0xffffll));
 }
-__device__ __forceinline__ float fq_load(const int *a)
+__device__ __forceinline__ float fq_load(const int *a, int fs)
 {
-    return fq_to_f((long long)a[0] * 65536ll + (long long)(unsigned)a[1]);
+    return fq_to_f((long long)a[0] * 65536ll + (long long)(unsigned)a[fs]);
 }
 
 // Everything after the pair sum for one owned bead at sorted slot g:
@@ -390,7 +391,10 @@ struct TilePlan {
 struct TileArrays {
     uint2 *X;          // fixed-point position
     float2 *v;         // velocity
-    int *f;            // force counts: (hi, lo) words of x, then of y
+    int *f;            // force counts, one array per word: x hi, x lo, y hi, y lo
+    int fs;            // words per array (the capacity): bead k's words are
+                       // f[k], f[fs + k], f[2 fs + k], f[3 fs + k], so the
+                       // atomics of a warp's 32 pairs spread over all banks
     uint32_t *id;
     uint32_t *cnt;     // interacting neighbours (COUNT only)
     unsigned char *lc; // local cell (lx | ly << 4) of an owned bead
@@ -404,6 +408,7 @@ __device__ __forceinline__ TileArrays tile_arrays(unsigned char *smem, int cap, 
     a.X = (uint2 *)p;
     a.v = (float2 *)(p + 8 * (size_t)cap);
     a.f = (int *)(p + 16 * (size_t)cap);
+    a.fs = cap;
     a.id = (uint32_t *)(p + 32 * (size_t)cap);
     a.cnt = (uint32_t *)(p + 36 * (size_t)cap);
     a.lc = p + (count ? 40 : 36) * (size_t)cap;
@@ -452,14 +457,14 @@ __device__ __forceinline__ void pairs_thread(const Sys &d, int n_own, int tw, in
                 fy += qy;
                 if (COUNT) ++cnt;
                 if (owned) {
-                    fq_add(&t.f[4 * j], -qx);
-                    fq_add(&t.f[4 * j + 2], -qy);
+                    fq_add(&t.f[j], t.fs, -qx);
+                    fq_add(&t.f[2 * t.fs + j], t.fs, -qy);
                     if (COUNT) atomicAdd(&t.cnt[j], 1u);
                 }
             }
         }
-        fq_add(&t.f[4 * k], fx);
-        fq_add(&t.f[4 * k + 2], fy);
+        fq_add(&t.f[k], t.fs, fx);
+        fq_add(&t.f[2 * t.fs + k], t.fs, fy);
         if (COUNT) atomicAdd(&t.cnt[k], cnt);
     }
 }
@@ -482,12 +487,12 @@ __device__ __forceinline__ void queue_eval(const Sys &d, uint32_t code, const Ti
     const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
     long long qx, qy;
     pair_force_q(d, t.X[k], t.X[j], t.v[k], t.v[j], t.id[k], t.id[j], s_lo, s_hi, qx, qy);
-    fq_add(&t.f[4 * k], qx);
-    fq_add(&t.f[4 * k + 2], qy);
+    fq_add(&t.f[k], t.fs, qx);
+    fq_add(&t.f[2 * t.fs + k], t.fs, qy);
     if (COUNT) atomicAdd(&t.cnt[k], 1u);
     if ((code >> 24) & 1u) {
-        fq_add(&t.f[4 * j], -qx);
-        fq_add(&t.f[4 * j + 2], -qy);
+        fq_add(&t.f[j], t.fs, -qx);
+        fq_add(&t.f[2 * t.fs + j], t.fs, -qy);
         if (COUNT) atomicAdd(&t.cnt[j], 1u);
     }
 }
@@ -905,12 +910,12 @@ __device__ __forceinline__ void queue_eval_g(const Sys &d, uint32_t code, const 
     const int k = code & 0xfffu, j = (code >> 12) & 0xfffu;
     long long qx, qy;
     pair_force_q(d, t.X[k], t.X[j], t.v[k], t.v[j], t.id[k], t.id[j], s_lo, s_hi, qx, qy);
-    fq_add(&t.f[4 * k], qx);
-    fq_add(&t.f[4 * k + 2], qy);
+    fq_add(&t.f[k], t.fs, qx);
+    fq_add(&t.f[2 * t.fs + k], t.fs, qy);
     if (COUNT) atomicAdd(&t.cnt[k], 1u);
     if (s_own[j]) {
-        fq_add(&t.f[4 * j], -qx);
-        fq_add(&t.f[4 * j + 2], -qy);
+        fq_add(&t.f[j], t.fs, -qx);
+        fq_add(&t.f[2 * t.fs + j], t.fs, -qy);
         if (COUNT) atomicAdd(&t.cnt[j], 1u);
     }
 }
@@ -1018,6 +1023,7 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
         t.X = (uint2 *)p;
         t.v = (float2 *)(p + 8 * (size_t)cap);
         t.f = (int *)(p + 16 * (size_t)cap);
+        t.fs = cap;
         t.id = (uint32_t *)(p + 32 * (size_t)cap);
         t.cnt = (uint32_t *)(p + 36 * (size_t)cap);   // COUNT only
         t.lc = nullptr;
@@ -1111,10 +1117,10 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
             t.X[s] = make_uint2(xv.x, xv.y);
             t.v[s] = make_float2(vbits(xv.z), vbits(xv.w));
             t.id[s] = d.S_id[g];
-            t.f[4 * s] = 0;
-            t.f[4 * s + 1] = 0;
-            t.f[4 * s + 2] = 0;
-            t.f[4 * s + 3] = 0;
+            t.f[s] = 0;
+            t.f[t.fs + s] = 0;
+            t.f[2 * t.fs + s] = 0;
+            t.f[3 * t.fs + s] = 0;
             if (COUNT) t.cnt[s] = 0u;
             s_own[s] = owned ? 1 : 0;
             if (owned) s_oslot[g - g0] = (uint16_t)s;
@@ -1134,7 +1140,7 @@ __device__ void force_tile_g(const Sys &d, int tile, int flags, unsigned char *s
             const uint32_t id = t.id[s];
             if (COUNT && d.pcnt) d.pcnt[id] = t.cnt[s];
             integrate_bead<B>(d, (int)g0 + k, make_uint4(x.x, x.y, fbits(v.x), fbits(v.y)), id,
-                              fq_load(&t.f[4 * s]), fq_load(&t.f[4 * s + 2]), flags, th);
+                              fq_load(&t.f[s], t.fs), fq_load(&t.f[2 * t.fs + s], t.fs), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
@@ -1269,10 +1275,10 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             t.X[k] = make_uint2(xv.x, xv.y);
             t.v[k] = make_float2(vbits(xv.z), vbits(xv.w));
             t.id[k] = d.S_id[g0 + k];
-            t.f[4 * k] = 0;
-            t.f[4 * k + 1] = 0;
-            t.f[4 * k + 2] = 0;
-            t.f[4 * k + 3] = 0;
+            t.f[k] = 0;
+            t.f[t.fs + k] = 0;
+            t.f[2 * t.fs + k] = 0;
+            t.f[3 * t.fs + k] = 0;
             if (COUNT) t.cnt[k] = 0u;
             t.lc[k] = (unsigned char)(lx | (ly << 4));
             if constexpr (TP::ORDER) {
@@ -1322,7 +1328,7 @@ __device__ void force_tile(const Sys &d, int tile, int flags, unsigned char *sme
             const uint4 xv = d.S_xv[g];
             const uint32_t id = t.id[k];
             if (COUNT && d.pcnt && id < (uint32_t)d.n) d.pcnt[id] = t.cnt[k];
-            integrate_bead<B>(d, g, xv, id, fq_load(&t.f[4 * k]), fq_load(&t.f[4 * k + 2]), flags, th);
+            integrate_bead<B>(d, g, xv, id, fq_load(&t.f[k], t.fs), fq_load(&t.f[2 * t.fs + k], t.fs), flags, th);
         }
     } else {
         force_tile_global<B, COUNT>(d, g0, n_own, s_lo, s_hi, flags, th);
